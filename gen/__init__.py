@@ -1,0 +1,23 @@
+"""Seeded synthetic inputs for the condensed-momentum solve.
+
+This package builds the inputs that both the CUDA library and the CPU oracle
+consume: the level matrices of the condensed momentum Jacobian (problem (1)
+of Section 4.2, with the solid deformation eliminated through the discrete
+relation d_t u = v of Eq. (defgrad) and the ALE derivatives dropped as in
+Eq. (REDUCEDMATRIX)), rediscretised on every multigrid level, plus the
+right-hand side and the Dirichlet mask.  It holds none of the solver's
+arithmetic (no matrix-vector product, smoother, transfer or Krylov step).
+"""
+
+from .q1fsi import (  # noqa: F401
+    Coefficients,
+    ConvectionField,
+    LevelMatrix,
+    Problem,
+    SyntheticSystem,
+    assemble_level,
+    build_system,
+    config_problem,
+    level_cells,
+    reference_element,
+)
