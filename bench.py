@@ -1,0 +1,347 @@
+"""Benchmark: time to 1e-8 relative residual of the multigrid-preconditioned
+FGMRES solve of the condensed momentum system on one GB300.
+
+One step = one complete solve (FGMRES(30) + one V(2,2) cycle per iteration,
+rtol 1e-8 on the FP64 true residual) of the 2d 256x256 Q1 workload
+(198,147 unknowns, 7 levels), V-cycle in FP32, outer FGMRES in FP64.  The
+right-hand side is resident in HBM when the timed region starts; the L2 is
+flushed (a 256 MB write) before every timed solve, outside the per-solve
+events.  The same solve through the C ABI with host buffers gives "e2e"; the
+plain FP64 path on the same mesh is timed beside it.
+
+--impl reference times the FP64 CPU oracle (same method, same workload) on
+the host cores instead.  Under torchrun (N > 1) every rank solves its own
+copy of the workload (replicas; the path has no exchange step).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual (mixed vs FP64 MG) and HBM GB/s; p50/p99 latency"
+WORKLOAD = "cfg2"
+WORKLOAD_DESC = ("2d 256x256 Q1 condensed-momentum Jacobian (198,147 unknowns), solid x>0.6, "
+                 "7 MG levels, V(2,2) Vanka 2x2-cell patches (27 unknowns), FGMRES(30) rtol 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nmg", choices=["nmg", "reference"])
+    ap.add_argument("--precision", type=int, default=1, help="V-cycle precision: 0 FP64, 1 FP32, 2 BF16")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ----------------------------------------------------------------------------
+
+CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+from gen import build_system, config_problem
+from oracle.solver import OracleSolver
+s = build_system(config_problem({wl!r}))
+o = OracleSolver(s.levels, s.dirichlet)
+times = []
+info = None
+for _ in range({reps}):
+    t = time.perf_counter()
+    x, info = o.solve(s.rhs, rtol=1e-8)
+    times.append(time.perf_counter() - t)
+print(json.dumps({{"times": times, "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+                   "setup_s": o.setup_seconds}}))
+"""
+
+
+def run_oracle(reps: int):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT, wl=WORKLOAD, reps=reps)],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    t0 = time.time()
+    res = run_oracle(args.warmup + args.steps)
+    times = res["times"][args.warmup:]
+    ms = 1000.0 * statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "solver": "FP64 CPU oracle (numpy/scipy), same method"},
+        "iterations": res["iterations"], "rel_residual": res["rel_residual"],
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full oracle solves of the workload (setup excluded), 1 thread"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.time() - t0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+
+    from gen import build_system, config_problem
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import Session, solve_opts
+
+    sysm = build_system(config_problem(WORKLOAD))
+    stream = torch.cuda.Stream()
+    prec_mask = (1 << nmg.NMG_PREC_FP64) | (1 << args.precision)
+    S = Session(2, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels], sysm.dirichlet,
+                precisions=prec_mask, stream=stream.cuda_stream)
+    n = sysm.unknowns
+    b = torch.from_numpy(sysm.rhs).cuda()
+    x = torch.empty_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    use_graph = 0 if args.no_graph else 1
+
+    def timed_solves(prec, k, graph, profile=False):
+        times, infos = [], []
+        if profile:
+            nmg.check(nmg.nmg_profile_enable(S.handle, 1))
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = S.solve(b, x, precision=prec, use_graph=graph)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                infos.append(info)
+        prof = None
+        if profile:
+            import ctypes as C
+            ms, cnt, bpl = C.c_double(), C.c_int64(), C.c_double()
+            nmg.check(nmg.nmg_profile_read(S.handle, ms, cnt, bpl))
+            nmg.check(nmg.nmg_profile_enable(S.handle, 0))
+            prof = (ms.value, cnt.value, bpl.value)
+        return times, infos, prof
+
+    # warm-up (also captures the V-cycle graphs)
+    timed_solves(args.precision, args.warmup, use_graph)
+    timed_solves(nmg.NMG_PREC_FP64, max(1, args.warmup // 2), use_graph)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    times, infos, _ = timed_solves(args.precision, args.steps, use_graph)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+
+    # dominant kernel (finest-level Vanka apply) timed with events on its launch stream
+    ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=True)
+    # plain FP64 path on the same mesh
+    t64, i64, _ = timed_solves(nmg.NMG_PREC_FP64, args.steps, use_graph)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    bh = torch.from_numpy(sysm.rhs.copy()).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        S.solve(bh, xh, precision=args.precision, use_graph=use_graph)
+        e2e.append(1000.0 * (time.perf_counter() - t))
+
+    ms = statistics.mean(times)
+    ms_tensor = torch.tensor([ms, wall], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_tensor, op=dist.ReduceOp.MAX)
+    ms_max, wall_max = ms_tensor.tolist()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = peaks()
+    kms, klaunch, kbytes = prof
+    achieved = kbytes / (kms / klaunch * 1e-3) / 1e9 if klaunch else None
+    xr = x.cpu().numpy()
+    line = {
+        "metric": METRIC,
+        "value": ms_max,
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * wall_max / args.steps,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f32+f64", 2: "bf16/f32+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "unknowns": n, "levels": sysm.problem.levels,
+                   "vcycle_precision": {0: "fp64", 1: "fp32", 2: "bf16 factors"}[args.precision],
+                   "outer": "fp64 FGMRES(30)", "cuda_graph": bool(use_graph),
+                   "l2": "flushed before every solve (256 MB write, outside the per-solve events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations": infos[-1].iterations,
+        "rel_residual": infos[-1].rel_residual,
+        "solves_per_s": world * 1000.0 / ms_max,
+        "p50_ms": statistics.median(times),
+        "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
+        "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
+                      "speedup_of_mixed": statistics.mean(t64) / ms},
+        "roofline": {"kernel": "finest-level Vanka apply (patch inverse GEMV)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
+                     "bytes_per_launch": kbytes,
+                     "timed": f"{klaunch} launches over {args.steps} solves with plain launches (events per launch)"},
+        "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": int(sum(i.launches for i in infos)),
+        "clocks": clk,
+    }
+    if not args.skip_cpu:
+        try:
+            res = run_oracle(1)
+            line["cpu_baseline"] = {"value": 1000.0 * res["times"][0], "unit": "ms", "cores": 1, "kind": "oracle",
+                                    "sample": "one full FP64 oracle solve of the same workload (setup excluded), "
+                                              "1 thread", "iterations": res["iterations"]}
+        except Exception as e:   # the GPU number stands without it
+            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    line["check"] = {"rel_residual_host": float(np.linalg.norm(sysm.rhs - _matvec(sysm, xr)) /
+                                                np.linalg.norm(sysm.rhs))}
+    print(json.dumps(line), flush=True)
+    S.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _matvec(sysm, x):
+    import scipy.sparse as sp
+    f = sysm.fine
+    nc = f.vals.shape[1]
+    A = sp.bsr_matrix((f.vals, f.col_idx, f.row_ptr), shape=(f.nodes * nc,) * 2)
+    return A @ x
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

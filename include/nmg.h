@@ -1,0 +1,201 @@
+/*
+ * nmg.h -- C ABI of libnmg, a GB300 (sm_103a) solver for the condensed momentum
+ * system of a monolithic Newton-multigrid fluid-structure solver
+ * (Failer & Richter, "A parallel Newton multigrid framework for monolithic
+ * fluid-structure interactions", arXiv:1904.02401).
+ *
+ * The linear problem is problem (1) of Section 4.2 (Eq. (problem:1)): velocity
+ * and pressure on the joint fluid/solid mesh after the solid deformation has
+ * been eliminated through the discrete relation d_t u = v (Eq. (defgrad)) and
+ * all ALE derivatives have been dropped (Eq. (REDUCEDMATRIX)).  It is solved as
+ * in Section 4.3: (I) an outer GMRES iteration, (II) preconditioned by one
+ * geometric multigrid V-cycle on nested meshes, (III) smoothed by the additive
+ * Vanka patch iteration of Eq. (vanka) with exactly inverted patch matrices.
+ *
+ * Conventions used by every call below.
+ *  - Meshes are uniform Cartesian Q1 meshes with n[k] cells per direction on
+ *    the finest level and half as many on each coarser level.  Nodes are
+ *    numbered lexicographically, x fastest.
+ *  - Vectors are node-blocked (Section 4.3): unknown (node, c) sits at index
+ *    node * ncomp + c, ncomp = dim + 1, component order (v_x, v_y[, v_z], p).
+ *  - Matrices are block-sparse rows (BSR) over nodes with ncomp x ncomp blocks
+ *    stored row-major (Section 4.3, "local blocks of size n_c x n_c"); every
+ *    block column must be a Q1 neighbour of its row (offsets in {-1,0,1}^dim).
+ *  - Levels are numbered 0 (coarsest) .. levels-1 (finest).
+ *  - All device work is ordered on the stream given in nmg_mesh_desc.  Calls
+ *    that return results to the host synchronise that stream before returning.
+ *  - Pointers named "device" must be device (or managed) memory; pointers
+ *    named "host or device" may be either, the library detects which.  The
+ *    caller owns every pointer it passes; the library copies what it keeps.
+ *  - Every call returns an nmg_status.  No C++ exception crosses the ABI.  On
+ *    error, nmg_last_error() returns a message for the calling thread.
+ */
+#ifndef NMG_H
+#define NMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int nmg_status;
+
+#define NMG_OK                  0
+#define NMG_PENDING             1   /* nmg_poll: the request is still running          */
+#define NMG_ERR_INVALID        -1   /* bad argument, size, pattern or call order        */
+#define NMG_ERR_OOM            -2   /* device allocation failed or memory budget refused */
+#define NMG_ERR_SINGULAR_PATCH -3   /* a Vanka patch matrix (or the coarse matrix) had a zero pivot */
+#define NMG_ERR_NOT_CONVERGED  -4   /* maxit reached before rtol                        */
+#define NMG_ERR_NONFINITE      -5   /* NaN or Inf met in the input or in a reduction    */
+#define NMG_ERR_TIMEOUT        -6   /* nmg_poll deadline passed                         */
+#define NMG_ERR_CUDA           -7   /* a CUDA runtime call failed                       */
+
+/* Arithmetic of the multigrid preconditioner (the outer FGMRES is always FP64). */
+#define NMG_PREC_FP64 0   /* matrices, patch inverses and V-cycle vectors in FP64        */
+#define NMG_PREC_FP32 1   /* FP32 matrices, patch inverses and V-cycle vectors           */
+#define NMG_PREC_BF16 2   /* BF16 patch inverses, FP32 matrices and vectors, FP32 sums   */
+
+/* How overlapping Vanka patch corrections are combined (Eq. (vanka)). */
+#define NMG_WEIGHT_AVERAGE 0  /* each unknown's summed correction divided by its patch count */
+#define NMG_WEIGHT_SUM     1  /* the plain sum as printed in Eq. (vanka)                     */
+
+typedef struct nmg_hierarchy nmg_hierarchy;
+typedef struct nmg_server nmg_server;
+
+typedef struct {
+    int dim;                        /* 2 or 3                                                      */
+    int n[3];                       /* finest-level cells per direction; n[2] ignored when dim==2 */
+    int levels;                     /* multigrid levels >= 1; n[k] divisible by 2^(levels-1) and,
+                                       above the coarsest level, even (patches of 2^dim cells)    */
+    int ncomp;                      /* must equal dim + 1                                          */
+    int patch_cells;                /* cells per patch direction; only 2 is supported              */
+    const uint8_t* dirichlet_mask;  /* host, one byte per finest-level unknown, 1 = Dirichlet;
+                                       coarse-level masks are taken by injection (node I <- 2I)   */
+    int precisions;                 /* bit mask (1 << NMG_PREC_*) of V-cycle precisions to prepare;
+                                       0 means FP64 | FP32 | BF16                                  */
+    size_t mem_budget_bytes;        /* 0 = unlimited; otherwise creation and set_jacobian fail with
+                                       NMG_ERR_OOM once the hierarchy would exceed it             */
+    void* stream;                   /* cudaStream_t used for all work on this hierarchy (NULL =
+                                       the legacy default stream); owned by the caller             */
+} nmg_mesh_desc;
+
+typedef struct {
+    double rtol;      /* stop when ||b - A x||_2 <= rtol ||b||_2 (true residual, FP64)            */
+    int restart;      /* FGMRES restart length m, 1..64                                           */
+    int maxit;        /* maximum total FGMRES iterations (preconditioner applications)            */
+    int nu1, nu2;     /* Vanka pre- and post-smoothing steps per level                            */
+    double omega;     /* Vanka damping omega_V (Section 4.3: about 0.8)                           */
+    int precision;    /* NMG_PREC_* of the V-cycle; must be among the prepared precisions          */
+    int weighting;    /* NMG_WEIGHT_*                                                             */
+    int use_graph;    /* 1: replay the V-cycle as a captured CUDA graph; 0: plain launches        */
+} nmg_solve_opts;
+
+typedef struct {
+    int iterations;       /* total FGMRES iterations                                      */
+    int restarts;         /* completed restart cycles beyond the first                    */
+    double rel_residual;  /* final true ||b - A x||_2 / ||b||_2, computed in FP64          */
+    double ms_total;      /* wall time of the call, milliseconds                           */
+    nmg_status status;    /* status of the solve (also the return value)                  */
+    int64_t launches;     /* CUDA kernels this solve launched (graph nodes counted each replay) */
+} nmg_solve_info;
+
+/* Fills *opts with rtol 1e-8, restart 30, maxit 1000, nu1 = nu2 = 2, omega 0.8,
+ * precision FP32, weighting AVERAGE, use_graph 1. */
+nmg_status nmg_default_opts(nmg_solve_opts* opts);
+
+/* Creates an empty hierarchy for the mesh in *desc (Section 4.3 (II): nested
+ * uniform meshes, one matrix per level).  *out receives an opaque handle owned
+ * by the library until nmg_destroy_hierarchy.  NMG_ERR_INVALID on a bad
+ * description, NMG_ERR_OOM if the vectors do not fit the budget. */
+nmg_status nmg_create_hierarchy(const nmg_mesh_desc* desc, nmg_hierarchy** out);
+
+/* Sets the matrix of one level (Section 4.3: block matrix A with n_c x n_c
+ * blocks; Section 5.5.2: a matrix is assembled on every level).  row_ptr has
+ * nrows_blk + 1 entries (nrows_blk = nodes of that level), col_idx and vals
+ * have nnzb blocks, vals row-major ncomp x ncomp per block, FP64.  ptr_location
+ * 0 = the three arrays are host memory, 1 = device memory.  The library copies
+ * and converts them; the caller keeps ownership.  On a level above the
+ * coarsest this also extracts every patch matrix A_i = R_i A R_i^T and inverts
+ * it exactly (LU-equivalent Gauss-Jordan with partial pivoting, FP64), all
+ * patches of the level in one launch; on level 0 it inverts the coarse matrix.
+ * NMG_ERR_INVALID for a wrong size, a column outside the Q1 stencil or a
+ * duplicate block; NMG_ERR_NONFINITE for NaN/Inf values;
+ * NMG_ERR_SINGULAR_PATCH for a zero pivot. */
+nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int64_t nnzb,
+                            const int64_t* row_ptr, const int32_t* col_idx, const double* vals,
+                            int ptr_location);
+
+/* Solves A x = b on the finest level with FGMRES(restart) right-preconditioned by
+ * one V(nu1, nu2)-cycle per iteration (Section 4.3 (I)-(III)).  b and x are
+ * FP64 vectors of ncomp * nodes entries, host or device; x need not be
+ * initialised (the initial guess is 0) and is overwritten.  Returns after the
+ * solve has completed.  info may be NULL.  NMG_ERR_NOT_CONVERGED if maxit was
+ * reached (x then holds the last iterate); NMG_ERR_NONFINITE if a norm became
+ * NaN/Inf; NMG_ERR_INVALID if a level matrix is missing. */
+nmg_status nmg_solve(nmg_hierarchy* h, const double* b, double* x, const nmg_solve_opts* opts,
+                     nmg_solve_info* info);
+
+/* ---- operator-level calls (one step of the method each; vectors are device
+ * arrays of the precision's arithmetic type: double for NMG_PREC_FP64, float
+ * for NMG_PREC_FP32 and NMG_PREC_BF16; sizes are ncomp * nodes of the level) */
+
+/* y = A_level x (Section 4.3 block matrix-vector product). */
+nmg_status nmg_matvec(nmg_hierarchy* h, int level, int precision, const void* x, void* y);
+
+/* r = b - A_level x. */
+nmg_status nmg_residual(nmg_hierarchy* h, int level, int precision, const void* b, const void* x,
+                        void* r);
+
+/* steps iterations of Eq. (vanka) on A_level x = b, in place on x (level >= 1).
+ * x_is_zero = 1 treats x as zero on entry (its contents are ignored). */
+nmg_status nmg_smooth(nmg_hierarchy* h, int level, int precision, const void* b, void* x, int steps,
+                      int x_is_zero, double omega, int weighting);
+
+/* r_coarse = P^T r_fine from level to level-1, Dirichlet entries of level-1 set to 0
+ * (Q1 full weighting, the transpose of nodal interpolation). */
+nmg_status nmg_restrict(nmg_hierarchy* h, int level, int precision, const void* r_fine,
+                        void* r_coarse);
+
+/* x_fine += P e_coarse from level-1 to level, Dirichlet entries of level left unchanged. */
+nmg_status nmg_prolongate_add(nmg_hierarchy* h, int level, int precision, const void* e_coarse,
+                              void* x_fine);
+
+/* x = A_0^{-1} b on the coarsest level (dense inverse computed in FP64 at set-up). */
+nmg_status nmg_coarse_solve(nmg_hierarchy* h, int precision, const void* b, void* x);
+
+/* z = one V(nu1, nu2)-cycle applied to r on the finest level, zero initial guess
+ * on every level (Section 4.3 (II)). */
+nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* r, void* z);
+
+/* Copies count patch inverses of a level, starting at patch first, to host
+ * memory out (count * n_p * n_p doubles, row-major A_i^{-1}, converted from the
+ * precision's storage type).  Patches are ordered by origin with x fastest;
+ * patch-local unknowns node-major over the 3^dim nodes (x fastest), then
+ * component. */
+nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int precision, int64_t first,
+                                  int64_t count, double* out);
+
+/* Bytes of device memory held by the hierarchy. */
+nmg_status nmg_hierarchy_bytes(nmg_hierarchy* h, size_t* bytes);
+
+/* Releases every device allocation of the hierarchy; h is invalid afterwards. */
+nmg_status nmg_destroy_hierarchy(nmg_hierarchy* h);
+
+/* ---- kernel timing: when enabled, the finest-level Vanka apply launches of
+ * later solves are bracketed by CUDA events on the hierarchy's stream. */
+nmg_status nmg_profile_enable(nmg_hierarchy* h, int enable);
+/* Total milliseconds and launch count of the timed launches since enabling,
+ * and the algorithmic bytes one such launch moves. */
+nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launches,
+                            double* bytes_per_launch);
+
+/* Thread-local description of the last error (never NULL). */
+const char* nmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMG_H */

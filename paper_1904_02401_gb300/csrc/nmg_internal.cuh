@@ -1,0 +1,170 @@
+// Internal declarations of libnmg: device data layout of a hierarchy and the
+// host-side launchers of every kernel.  Nothing here crosses the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nmg.h"
+
+namespace nmg {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxRestart = 64;
+constexpr int kDotBlocks = 296;        // fixed grid of the deterministic reductions (2 x 148)
+
+// ---------------------------------------------------------------------------
+// Structured level geometry (uniform Q1 mesh, nodes x fastest)
+// ---------------------------------------------------------------------------
+struct Geom {
+    int dim;
+    int nc;            // components per node = dim + 1
+    int cells[3];      // cells per direction (1 in unused directions)
+    int nn[3];         // nodes per direction (1 in unused directions)
+    int64_t nodes;     // nn[0] * nn[1] * nn[2]
+    int64_t ld;        // leading dimension of the stencil arrays (nodes rounded up to 32)
+    int pc[3];         // patches per direction (cells / 2)
+    int64_t patches;
+    int np;            // unknowns per patch = 3^dim * nc
+    int nst;           // stencil positions 3^dim
+};
+
+// Matrix of one level in "stencil" layout: for stencil position s (offset
+// o(s) in {-1,0,1}^dim, s = sum (o_k + 1) 3^k) and block entry e = r * nc + c,
+// value A[(s * nc * nc + e) * ld + node].  Out-of-mesh neighbours hold zero.
+// Structure-of-arrays per (s, e) makes every warp load of the matrix one
+// contiguous, coalesced segment.
+
+template <typename T> struct VTypes;   // vector arithmetic type per storage precision
+
+struct PrecData {                 // per-precision data of one level
+    void* A = nullptr;            // stencil matrix in the arithmetic type (double / float)
+    void* inv = nullptr;          // patch inverses, column-major n_p x n_p, padded stride
+    int64_t inv_stride = 0;       // elements between consecutive patch inverses
+    void* b = nullptr;            // V-cycle work vectors of the level (arithmetic type)
+    void* x = nullptr;
+    void* r = nullptr;
+    void* corr = nullptr;         // per-patch corrections A_i^{-1} R_i d, patches * n_p
+};
+
+struct Level {
+    Geom g;
+    bool ready = false;
+    double* A64 = nullptr;        // FP64 stencil matrix (always kept: outer FGMRES + FP64 mode)
+    uint8_t* mask = nullptr;      // Dirichlet flag per unknown
+    PrecData p[3];                // NMG_PREC_FP64 / FP32 / BF16
+};
+
+struct Hierarchy {
+    nmg_mesh_desc desc;
+    int dim = 0, nc = 0, L = 0;
+    int prec_mask = 0;
+    cudaStream_t stream = nullptr;
+    Level lev[kMaxLevels];
+    // coarse level dense inverse (FP64), n0 x n0 row-major
+    double* coarse_inv = nullptr;
+    int64_t n0 = 0;
+    // outer FGMRES (FP64) workspace on the finest level
+    double* b64 = nullptr;        // right-hand side copy
+    double* x64 = nullptr;        // iterate
+    double* w64 = nullptr;        // Arnoldi vector
+    double* V = nullptr;          // (m + 1) Krylov vectors
+    double* Z = nullptr;          // m preconditioned vectors
+    double* partial = nullptr;    // kMaxRestart + 2 rows of kDotBlocks partial sums
+    double* scal = nullptr;       // device scalars (see krylov kernels)
+    double* host_scal = nullptr;  // pinned mirror of a few scalars
+    int* flags = nullptr;         // device error flags
+    int m_alloc = 0;
+    size_t bytes = 0;
+    // CUDA graphs of the V-cycle, per precision (rebuilt when options change)
+    cudaGraphExec_t vgraph[3] = {nullptr, nullptr, nullptr};
+    int vgraph_key[3][4] = {};    // nu1, nu2, weighting, omega bits hash
+    double vgraph_omega[3] = {0, 0, 0};
+    // profiling of the finest-level Vanka apply
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;   // pairs
+    int prof_used = 0;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    int64_t launches = 0;               // kernels enqueued (graph nodes counted per replay)
+    int64_t vgraph_nodes[3] = {0, 0, 0};
+    double prof_bytes = 0.0;
+    std::vector<void*> allocs;
+};
+
+// Error flags (device int array)
+enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_COUNT = 4 };
+
+// ---------------------------------------------------------------------------
+// Launchers (setup_kernels.cu)
+// ---------------------------------------------------------------------------
+void launch_bsr_to_stencil(const Geom& g, const int64_t* row_ptr, const int32_t* col_idx,
+                           const double* vals, int64_t nnzb, double* A64, int* flags, cudaStream_t s);
+void launch_convert_f64_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_patch_invert(const Geom& g, const double* A64, double* inv64, int64_t s64,
+                                float* inv32, int64_t s32, __nv_bfloat16* invbf, int64_t sbf,
+                                int* flags, cudaStream_t s);
+void launch_coarse_assemble(const Geom& g, const double* A64, double* dense, cudaStream_t s);
+void launch_dense_invert(double* a, int64_t n, int* perm, int* flags, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Launchers (smooth_kernels.cu); T = double or float
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual,
+                 cudaStream_t s);
+template <typename T, typename TS>
+void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr,
+                        cudaStream_t s);
+template <typename T>
+void launch_vanka_update(const Geom& g, const T* corr, T* x, bool x_zero, T omega, bool average,
+                         cudaStream_t s);
+template <typename T>
+void launch_restrict(const Geom& fine, const Geom& coarse, const T* rf, T* rc,
+                     const uint8_t* cmask, cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const Geom& fine, const Geom& coarse, const T* ec, T* xf,
+                        const uint8_t* fmask, cudaStream_t s);
+template <typename T>
+void launch_coarse_gemv(const double* inv, int64_t n, const T* b, T* x, cudaStream_t s);
+template <typename TI, typename TO>
+void launch_convert(const TI* in, TO* out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Launchers (krylov_kernels.cu): FP64 outer FGMRES
+// ---------------------------------------------------------------------------
+// scal layout (doubles):
+enum Scal {
+    S_BNORM = 0, S_BETA = 1, S_EST = 2, S_INVH = 3, S_STATUS = 4, S_ITER = 5,
+    S_H = 8,                                   // (m+1) x m Hessenberg, column-major, ld m+1
+    S_CS = S_H + (kMaxRestart + 1) * kMaxRestart,
+    S_SN = S_CS + kMaxRestart,
+    S_G = S_SN + kMaxRestart,
+    S_Y = S_G + kMaxRestart + 1,
+    S_HC = S_Y + kMaxRestart,                  // current column h_{0..j}
+    S_COUNT = S_HC + kMaxRestart + 2
+};
+void launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
+void launch_multidot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
+                     double* partial, double* out, bool accumulate, cudaStream_t s);
+void launch_gs_update(const double* V, int64_t ldv, int nvec, const double* h, double* w,
+                      int64_t n, double* partial, double* nrm2, bool want_norm, cudaStream_t s);
+void launch_arnoldi_finish(double* scal, int j, int m, cudaStream_t s);
+void launch_scale(const double* x, const double* scal_ptr, bool invert, double* y, int64_t n,
+                  cudaStream_t s);
+void launch_start_cycle(double* scal, int m, cudaStream_t s);
+void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x,
+                         int64_t n, cudaStream_t s);
+void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
+
+}  // namespace nmg
+
+namespace nmg {
+// Kernels enqueued by the calling thread (launchers add to it; a graph replay
+// adds the number of kernel nodes it holds).
+extern thread_local int64_t g_launches;
+}  // namespace nmg
