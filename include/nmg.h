@@ -191,6 +191,30 @@ nmg_status nmg_profile_enable(nmg_hierarchy* h, int enable);
 nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launches,
                             double* bytes_per_launch);
 
+/* ---- one Vanka correction that allocates no device memory.  The paper has no
+ * counterpart: this call exists for callers that cannot let a library call
+ * cudaMalloc, such as code that manages all device memory in its own fixed
+ * arena, or a hot loop where cudaMalloc (which can synchronise the device and
+ * is not stream-ordered) is not allowed.  It needs no hierarchy; the caller
+ * passes every input and output:
+ *   x <- (x_is_zero ? 0 : x) + omega * W * sum_i R_i^T A_i^{-1} R_i d
+ * on a level with cells[0..dim-1] cells (each even), W as in weighting.
+ * inv: device patch inverses in the library's layout (patch i at element
+ * i * inv_stride, column-major n_p x n_p, n_p = 3^dim (dim+1); storage double,
+ * float or bfloat16 for precision FP64, FP32, BF16; inv_stride >= n_p^2).
+ * d, x: device vectors of (dim+1) * nodes entries, double for FP64, float
+ * otherwise.  Work is enqueued on stream (a cudaStream_t; NULL = the legacy
+ * default stream) and the call returns without waiting for it.
+ * The per-patch scratch lives in one fixed 16 MiB device array of the library
+ * (patches * n_p * sizeof(element) must fit, else NMG_ERR_INVALID), which
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race with each other. */
+nmg_status nmg_vanka_correct_noalloc(int dim, const int* cells, int precision, const void* inv,
+                                     int64_t inv_stride, const void* d, void* x, double omega,
+                                     int weighting, int x_is_zero, void* stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char* nmg_last_error(void);
 

@@ -102,6 +102,8 @@ _SIGS = {
     "nmg_destroy_hierarchy": [_H],
     "nmg_profile_enable": [_H, C.c_int],
     "nmg_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "nmg_vanka_correct_noalloc": [C.c_int, C.POINTER(C.c_int), C.c_int, _P, C.c_int64, _P, _P, C.c_double,
+                                  C.c_int, C.c_int, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -198,3 +200,10 @@ def nmg_profile_enable(h, enable) -> int:
 
 def nmg_profile_read(h, ms: C.c_double, launches: C.c_int64, bytes_per_launch: C.c_double) -> int:
     return _lib.nmg_profile_read(h, C.byref(ms), C.byref(launches), C.byref(bytes_per_launch))
+
+
+def nmg_vanka_correct_noalloc(dim, cells, precision, inv, inv_stride, d, x, omega, weighting, x_is_zero,
+                              stream=None) -> int:
+    c = (C.c_int * 3)(*(list(cells) + [0] * (3 - len(cells))))
+    return _lib.nmg_vanka_correct_noalloc(dim, c, precision, ptr(inv), inv_stride, ptr(d), ptr(x), omega,
+                                          weighting, x_is_zero, stream)
