@@ -29,9 +29,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-8 rel. residual (mixed vs FP64 MG) and HBM GB/s; p50/p99 latency"
+WORKLOADS = {
+    "cfg2": ("2d 256x256 Q1 condensed-momentum Jacobian (198,147 unknowns), solid x>0.6, "
+             "7 MG levels, V(2,2) Vanka 2x2-cell patches (27 unknowns), FGMRES(30) rtol 1e-8"),
+    "cfg3": ("3d 32^3 Q1 condensed-momentum Jacobian (143,748 unknowns), solid z<0.25, "
+             "4 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
+    "cfg4": ("3d 96^3 Q1 condensed-momentum Jacobian (3,650,692 unknowns), solid z<0.25, "
+             "6 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
+}
 WORKLOAD = "cfg2"
-WORKLOAD_DESC = ("2d 256x256 Q1 condensed-momentum Jacobian (198,147 unknowns), solid x>0.6, "
-                 "7 MG levels, V(2,2) Vanka 2x2-cell patches (27 unknowns), FGMRES(30) rtol 1e-8")
+WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 
 
 def parse():
@@ -43,6 +50,11 @@ def parse():
     ap.add_argument("--precision", type=int, default=1, help="V-cycle precision: 0 FP64, 1 FP32, 2 BF16")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving workload: Poisson stream of solves over resident 2d/3d hierarchies")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS),
+                    help="cfg2 is the measured workload; the others are for investigation")
     return ap.parse_args()
 
 
@@ -195,7 +207,7 @@ def gpu_arm(args):
     sysm = build_system(config_problem(WORKLOAD))
     stream = torch.cuda.Stream()
     prec_mask = (1 << nmg.NMG_PREC_FP64) | (1 << args.precision)
-    S = Session(2, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels], sysm.dirichlet,
+    S = Session(sysm.problem.dim, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels], sysm.dirichlet,
                 precisions=prec_mask, stream=stream.cuda_stream)
     n = sysm.unknowns
     b = torch.from_numpy(sysm.rhs).cuda()
@@ -244,8 +256,8 @@ def gpu_arm(args):
         dist.barrier()
     clk = clocks.stop()
 
-    # dominant kernel (finest-level Vanka apply) timed with events on its launch stream
-    ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=True)
+    # the V-cycle (the dominant launch) timed with events on its launch stream, same configuration
+    ptimes, pinfos, prof = timed_solves(args.precision, args.steps, use_graph, profile=True)
     # plain FP64 path on the same mesh
     t64, i64, _ = timed_solves(nmg.NMG_PREC_FP64, args.steps, use_graph)
 
@@ -294,18 +306,20 @@ def gpu_arm(args):
                    "l2": "flushed before every solve (256 MB write, outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": infos[-1].iterations,
+        "engine": {1: "kernels", 2: "persistent"}.get(infos[-1].engine, "?"),
         "rel_residual": infos[-1].rel_residual,
         "solves_per_s": world * 1000.0 / ms_max,
         "p50_ms": statistics.median(times),
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
                       "speedup_of_mixed": statistics.mean(t64) / ms},
-        "roofline": {"kernel": "finest-level Vanka apply (patch inverse GEMV)", "bound": "hbm",
+        "roofline": {"kernel": ("V-cycle: one persistent cooperative kernel" if infos[-1].engine == 2 else
+                                "V-cycle: CUDA graph of per-step kernels"), "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
-                     "timed": f"{klaunch} launches over {args.steps} solves with plain launches (events per launch)"},
+                     "timed": f"{klaunch} V-cycles over {args.steps} solves (events around each V-cycle)"},
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.launches for i in infos)),
@@ -335,8 +349,116 @@ def _matvec(sysm, x):
     return A @ x
 
 
+def serving_arm(args):
+    """Continuous-batching serving of condensed-momentum solves.
+
+    Meshes uniform over 2d {64^2, 128^2, 256^2, 512^2} and 3d {16^3, 32^3,
+    64^3} (50/50 between 2d and 3d); each mesh size has a pool of two resident
+    hierarchies (coefficient seeds 10 and 12); request i draws its mesh and
+    hierarchy from numpy default_rng(2) and its right-hand side from the CUDA
+    generator seeded 11 + 2 i.  Arrivals are a Poisson stream (seed 2) at 80%
+    of the saturated throughput measured first on a burst of the same mix.
+    """
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from gen import Problem, build_system
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import Session, solve_opts
+
+    torch.cuda.set_device(0)
+    sizes = [(2, 64), (2, 128), (2, 256), (2, 512), (3, 16), (3, 32), (3, 64)]
+    pool = []
+    t0 = time.time()
+    for dim, n in sizes:
+        for cseed in (10, 12):
+            levels = int(np.log2(n)) - 1
+            p = Problem(dim=dim, n=(n,) * dim, levels=levels,
+                        solid=(0, +1, 0.6) if dim == 2 else (2, -1, 0.25), conv_seed=cseed)
+            sy = build_system(p)
+            S = Session(dim, p.n, [(l.row_ptr, l.col_idx, l.vals) for l in sy.levels], sy.dirichlet,
+                        precisions=1 << nmg.NMG_PREC_FP32)
+            mask = torch.from_numpy(sy.dirichlet.astype(bool)).cuda()
+            pool.append((dim, n, S, mask))
+            del sy
+    setup_s = time.time() - t0
+    rng = np.random.default_rng(2)
+    opts = solve_opts(precision=nmg.NMG_PREC_FP32, engine=nmg.NMG_ENGINE_KERNELS)
+    budget = 150 * 10**9
+
+    def make_requests(count, seed0):
+        out = []
+        for i in range(count):
+            d2 = rng.random() < 0.5
+            cands = [k for k, (dim, n, S, m) in enumerate(pool) if (dim == 2) == d2]
+            k = int(rng.choice(cands))
+            dim, n, S, mask = pool[k]
+            g = torch.Generator(device="cuda").manual_seed(seed0 + 2 * i)
+            b = torch.rand(mask.numel(), dtype=torch.float64, device="cuda", generator=g) * 2.0 - 1.0
+            b[mask] = 0.0
+            out.append((k, b, torch.zeros_like(b)))
+        torch.cuda.synchronize()
+        return out
+
+    def run(reqs, rate):
+        server = C.c_void_p()
+        nmg.check(nmg.nmg_server_create(budget, 16, server))
+        tickets = []
+        start = time.perf_counter()
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
+        for (k, b, x), at in zip(reqs, arrivals):
+            now = time.perf_counter() - start
+            if at > now:
+                time.sleep(at - now)
+            t = C.c_uint64()
+            nmg.check(nmg.nmg_submit(server, pool[k][2].handle, b, x, opts, t))
+            tickets.append(t.value)
+        lat, its, bad = [], [], 0
+        for t in tickets:
+            info = nmg.nmg_solve_info()
+            st = nmg.nmg_poll(server, t, 600000, info)
+            bad += st != 0
+            lat.append(info.ms_total)
+            its.append(info.iterations)
+        wall = time.perf_counter() - start
+        nmg.nmg_server_destroy(server)
+        return wall, lat, its, bad
+
+    burst = make_requests(200, 1_000_011)
+    run(burst[:20], 0)                       # warm-up (graphs captured, engines resolved)
+    wall_b, _, _, _ = run(burst, 0)
+    saturated = len(burst) / wall_b
+    del burst
+    reqs = make_requests(args.requests, 11)
+    rate = 0.8 * saturated
+    wall, lat, its, bad = run(reqs, rate)
+    lat_sorted = sorted(lat)
+    line = {
+        "metric": METRIC, "value": statistics.median(lat), "unit": "ms (p50 submit-to-completion latency)",
+        "n_gpus": 1, "steps": len(reqs), "warmup": 20, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving: Poisson stream of condensed-momentum solves, 2d 64^2-512^2 and 3d "
+                               "16^3-64^3 (50/50), 14 resident hierarchies, FP32 V-cycle / FP64 FGMRES(30), "
+                               "rtol 1e-8, memory budget 150 GB, 16 slots",
+                   "arrival_rate_per_s": rate, "saturated_solves_per_s": saturated},
+        "p50_ms": statistics.median(lat), "p99_ms": lat_sorted[max(0, int(0.99 * len(lat)) - 1)],
+        "solves_per_s": len(reqs) / wall, "failed": bad, "mean_iterations": statistics.mean(its),
+        "setup_s": setup_s,
+    }
+    print(json.dumps(line), flush=True)
+    for _, _, S, _ in pool:
+        S.close()
+
+
 def main():
+    global WORKLOAD, WORKLOAD_DESC
     args = parse()
+    WORKLOAD, WORKLOAD_DESC = args.workload, WORKLOADS[args.workload]
+    if args.serving:
+        serving_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

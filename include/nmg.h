@@ -90,7 +90,13 @@ typedef struct {
     int precision;    /* NMG_PREC_* of the V-cycle; must be among the prepared precisions          */
     int weighting;    /* NMG_WEIGHT_*                                                             */
     int use_graph;    /* 1: replay the V-cycle as a captured CUDA graph; 0: plain launches        */
+    int engine;       /* NMG_ENGINE_*: how a V-cycle is executed                                  */
 } nmg_solve_opts;
+
+/* V-cycle execution engines (same arithmetic, same results). */
+#define NMG_ENGINE_AUTO       0  /* time both engines on this hierarchy at first use, keep the faster */
+#define NMG_ENGINE_KERNELS    1  /* one kernel per step (optionally replayed as a CUDA graph)         */
+#define NMG_ENGINE_PERSISTENT 2  /* one cooperative persistent kernel per V-cycle                     */
 
 typedef struct {
     int iterations;       /* total FGMRES iterations                                      */
@@ -99,10 +105,11 @@ typedef struct {
     double ms_total;      /* wall time of the call, milliseconds                           */
     nmg_status status;    /* status of the solve (also the return value)                  */
     int64_t launches;     /* CUDA kernels this solve launched (graph nodes counted each replay) */
+    int engine;           /* NMG_ENGINE_KERNELS or NMG_ENGINE_PERSISTENT, the engine used     */
 } nmg_solve_info;
 
 /* Fills *opts with rtol 1e-8, restart 30, maxit 1000, nu1 = nu2 = 2, omega 0.8,
- * precision FP32, weighting AVERAGE, use_graph 1. */
+ * precision FP32, weighting AVERAGE, use_graph 1, engine AUTO. */
 nmg_status nmg_default_opts(nmg_solve_opts* opts);
 
 /* Creates an empty hierarchy for the mesh in *desc (Section 4.3 (II): nested
@@ -136,6 +143,31 @@ nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int6
  * NaN/Inf; NMG_ERR_INVALID if a level matrix is missing. */
 nmg_status nmg_solve(nmg_hierarchy* h, const double* b, double* x, const nmg_solve_opts* opts,
                      nmg_solve_info* info);
+
+/* ---- serving: many solves of problem (1), one per Newton step of different
+ * simulations (Section 4.2, Eq. (newton): every Newton step solves one linear
+ * problem), batched continuously on resident hierarchies.
+ *
+ * nmg_server_create starts a server with a memory budget (bytes of resident
+ * hierarchies whose requests may run at once; 0 = unlimited) and at most
+ * max_slots requests in flight.  nmg_submit queues a solve of A x = b on
+ * hierarchy h and returns a ticket at once; b and x (FP64, host or device, b
+ * ready when submitted) must stay valid until the request completes.  A
+ * request starts when a slot is free, its hierarchy runs no other request and
+ * the budget allows; running requests advance concurrently on their
+ * hierarchies' streams, so requests that arrive while others run join them.
+ * Results equal those of nmg_solve.  nmg_poll returns NMG_PENDING at once
+ * (timeout_ms <= 0) or waits up to timeout_ms and then returns NMG_ERR_TIMEOUT;
+ * once a request is done it returns the solve's status, fills *info (ms_total
+ * = submit-to-completion latency) and releases the ticket.  Do not call
+ * nmg_solve on a hierarchy while the server may run a request on it.
+ * NMG_ERR_OOM from nmg_submit if h alone exceeds the budget. */
+nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server** out);
+nmg_status nmg_submit(nmg_server* s, nmg_hierarchy* h, const double* b, double* x,
+                      const nmg_solve_opts* opts, uint64_t* ticket);
+nmg_status nmg_poll(nmg_server* s, uint64_t ticket, int timeout_ms, nmg_solve_info* info);
+/* Finishes every queued and running request, then stops the server. */
+nmg_status nmg_server_destroy(nmg_server* s);
 
 /* ---- operator-level calls (one step of the method each; vectors are device
  * arrays of the precision's arithmetic type: double for NMG_PREC_FP64, float

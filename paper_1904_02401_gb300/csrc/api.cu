@@ -121,13 +121,6 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         cudaMemsetAsync(x, 0, g.nodes * g.nc * sizeof(T), s);
         return;
     }
-    const bool prof = h->prof && l == h->L - 1;
-    if (prof) {
-        const double sv = (double)sizeof(T);
-        const double si = prec == NMG_PREC_FP64 ? 8.0 : prec == NMG_PREC_FP32 ? 4.0 : 2.0;
-        h->prof_bytes = (double)g.patches * g.np * g.np * si + (double)g.nodes * g.nc * sv +
-                        (double)g.patches * g.np * sv;
-    }
     for (int st = 0; st < steps; ++st) {
         const T* d;
         if (st == 0 && x_zero) {
@@ -136,8 +129,6 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
             launch_spmv<T>(g, (const T*)P.A, x, b, (T*)P.r, true, s);
             d = (const T*)P.r;
         }
-        const bool rec = prof && h->prof_used < (int)h->prof_ev.size() / 2;
-        if (rec) cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
         if (prec == NMG_PREC_FP64)
             launch_vanka_apply<double, double>(g, (const double*)P.inv, P.inv_stride, (const double*)d, (double*)P.corr, s);
         else if (prec == NMG_PREC_FP32)
@@ -145,10 +136,6 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         else
             launch_vanka_apply<float, __nv_bfloat16>(g, (const __nv_bfloat16*)P.inv, P.inv_stride, (const float*)d,
                                                     (float*)P.corr, s);
-        if (rec) {
-            cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
-            h->prof_used++;
-        }
         launch_vanka_update<T>(g, (const T*)P.corr, x, st == 0 && x_zero, omega, average, s);
     }
 }
@@ -226,31 +213,137 @@ static nmg_status validate_opts(const nmg_solve_opts* o) {
     if (!o) return fail(NMG_ERR_INVALID, "opts is NULL");
     if (!(o->rtol >= 0.0) || o->restart < 1 || o->restart > kMaxRestart || o->maxit < 0 || o->nu1 < 0 ||
         o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64 || !std::isfinite(o->omega) ||
-        (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM))
+        (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM) ||
+        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_PERSISTENT)
         return fail(NMG_ERR_INVALID, "invalid solve options");
+    return NMG_OK;
+}
+
+// Algorithmic bytes of one V(nu1, nu2) cycle: on every smoothed level each
+// smoothing step reads all patch inverses once and writes / reads the
+// per-patch corrections, each residual reads the matrix once, and the vector
+// traffic of residual (x, b, r), update (x) and transfers is counted once per
+// step; the coarse solve reads its dense inverse.  (Unique bytes a perfect
+// implementation must move; reuse through the L2 can make a measured rate
+// exceed the HBM copy rate on levels that fit in the L2.)
+static double vcycle_bytes(const Hierarchy* h, int prec, int nu1, int nu2) {
+    const double sv = prec == NMG_PREC_FP64 ? 8.0 : 4.0;
+    const double si = prec == NMG_PREC_FP64 ? 8.0 : prec == NMG_PREC_FP32 ? 4.0 : 2.0;
+    double bytes = (double)h->n0 * h->n0 * 8.0 + 2.0 * h->n0 * sv;
+    for (int l = 1; l < h->L; ++l) {
+        const Geom& g = h->lev[l].g;
+        const double n = (double)g.nodes * g.nc;
+        const double mat = (double)g.nst * g.nc * g.nc * g.nodes * sv;
+        const double inv = (double)g.patches * g.np * g.np * si;
+        const double corr = (double)g.patches * g.np * sv;
+        const int steps = nu1 + nu2;
+        const int residuals = (nu1 > 0 ? nu1 - 1 : 0) + 1 + nu2;
+        bytes += steps * (inv + 2.0 * corr + 3.0 * n) + residuals * (mat + 3.0 * n);
+        const Geom& c = h->lev[l - 1].g;
+        bytes += 2.0 * (n + (double)c.nodes * c.nc);   // restriction and prolongation
+    }
+    return bytes;
+}
+
+// One V-cycle on the finest level's buffers (b -> x) with the given engine.
+static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) {
+    const int prec = o.precision;
+    if (engine == NMG_ENGINE_PERSISTENT) {
+        NMG_CK(launch_vcycle_persistent(h, prec, o.nu1, o.nu2, o.omega, o.weighting, h->pbar, h->flags + FLAG_ABORT,
+                                        64));
+        return NMG_OK;
+    }
+    if (o.use_graph) return vcycle_graph(h, prec, o);
+    vcycle_dispatch(h, prec, o, nullptr, nullptr);
+    return NMG_OK;
+}
+
+// Engine for these options: AUTO times both engines on this hierarchy (the
+// finest right-hand side zeroed, so the traffic is the real one) and keeps
+// the faster; the choice is cached per precision and (nu1, nu2, weighting).
+static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* engine) {
+    if (o.engine != NMG_ENGINE_AUTO) {
+        *engine = o.engine;
+        return NMG_OK;
+    }
+    const int prec = o.precision;
+    const int key[3] = {o.nu1, o.nu2, o.weighting};
+    if (h->engine_choice[prec] && std::memcmp(key, h->engine_key[prec], sizeof(key)) == 0) {
+        *engine = h->engine_choice[prec];
+        return NMG_OK;
+    }
+    Level& F = h->lev[h->L - 1];
+    const size_t vs = prec == NMG_PREC_FP64 ? sizeof(double) : sizeof(float);
+    NMG_CK(cudaMemsetAsync(F.p[prec].b, 0, F.g.nodes * F.g.nc * vs, h->stream));
+    cudaEvent_t e0, e1;
+    NMG_CK(cudaEventCreate(&e0));
+    NMG_CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int pick = NMG_ENGINE_KERNELS;
+    const int64_t launches0 = g_launches;
+    for (int eng = NMG_ENGINE_KERNELS; eng <= NMG_ENGINE_PERSISTENT; ++eng) {
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) ok = run_engine(h, o, eng) == NMG_OK;
+        cudaEventRecord(e0, h->stream);
+        for (int rep = 0; rep < 5 && ok; ++rep) ok = run_engine(h, o, eng) == NMG_OK;
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+        float ms = 0.f;
+        if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+            h->engine_us[prec][eng - 1] = 1000.0 * ms / 5.0;
+            if (ms < best) { best = ms; pick = eng; }
+        } else {
+            h->engine_us[prec][eng - 1] = -1.0;
+        }
+        cudaGetLastError();
+    }
+    g_launches = launches0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int f[FLAG_COUNT];
+    NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f[FLAG_ABORT]) {   // a persistent trial aborted: never pick it
+        NMG_CK(cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int)));
+        pick = NMG_ENGINE_KERNELS;
+    }
+    h->engine_choice[prec] = pick;
+    std::memcpy(h->engine_key[prec], key, sizeof(key));
+    *engine = pick;
+    return NMG_OK;
+}
+
+// z = V-cycle(v) for vectors of the precision's arithmetic type or FP64 (converted).
+static nmg_status vcycle_any(Hierarchy* h, const nmg_solve_opts& o, const void* v, void* z, bool fp64_io) {
+    Level& F = h->lev[h->L - 1];
+    const int64_t n = F.g.nodes * F.g.nc;
+    const int prec = o.precision;
+    int engine = 0;
+    NMG_TRY(resolve_engine(h, o, &engine));
+    if (prec == NMG_PREC_FP64 && engine == NMG_ENGINE_KERNELS && !o.use_graph && !h->prof) {
+        run_vcycle<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, (const double*)v, (double*)z);
+        return NMG_OK;
+    }
+    const size_t vs = prec == NMG_PREC_FP64 ? sizeof(double) : sizeof(float);
+    if (prec != NMG_PREC_FP64 && fp64_io) launch_convert<double, float>((const double*)v, (float*)F.p[prec].b, n, h->stream);
+    else NMG_CK(cudaMemcpyAsync(F.p[prec].b, v, n * vs, cudaMemcpyDeviceToDevice, h->stream));
+    const bool rec = h->prof && h->prof_used < (int)h->prof_ev.size() / 2;
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
+        h->prof_bytes = vcycle_bytes(h, prec, o.nu1, o.nu2);
+    }
+    NMG_TRY(run_engine(h, o, engine));
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], h->stream);
+        h->prof_used++;
+    }
+    if (prec != NMG_PREC_FP64 && fp64_io) launch_convert<float, double>((const float*)F.p[prec].x, (double*)z, n, h->stream);
+    else NMG_CK(cudaMemcpyAsync(z, F.p[prec].x, n * vs, cudaMemcpyDeviceToDevice, h->stream));
     return NMG_OK;
 }
 
 // z_j = M^{-1} v_j for FP64 vectors v, z on the finest level.
 static nmg_status precondition(Hierarchy* h, const nmg_solve_opts& o, const double* v, double* z) {
-    Level& F = h->lev[h->L - 1];
-    const int64_t n = F.g.nodes * F.g.nc;
-    const int prec = o.precision;
-    if (prec == NMG_PREC_FP64) {
-        if (o.use_graph) {
-            NMG_CK(cudaMemcpyAsync(F.p[prec].b, v, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-            NMG_TRY(vcycle_graph(h, prec, o));
-            NMG_CK(cudaMemcpyAsync(z, F.p[prec].x, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-        } else {
-            run_vcycle<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, v, z);
-        }
-    } else {
-        launch_convert<double, float>(v, (float*)F.p[prec].b, n, h->stream);
-        if (o.use_graph) NMG_TRY(vcycle_graph(h, prec, o));
-        else run_vcycle<float>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, nullptr, nullptr);
-        launch_convert<float, double>((const float*)F.p[prec].x, z, n, h->stream);
-    }
-    return NMG_OK;
+    return vcycle_any(h, o, v, z, true);
 }
 
 static nmg_status ensure_krylov(Hierarchy* h, int m) {
@@ -278,78 +371,230 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static nmg_status solve_impl(Hierarchy* h, const double* b_user, double* x_user, const nmg_solve_opts& o,
-                             nmg_solve_info* info) {
-    auto t0 = std::chrono::steady_clock::now();
-    const int64_t launches0 = g_launches;
-    NMG_TRY(check_ready(h, o.precision));
-    NMG_TRY(ensure_krylov(h, o.restart));
+struct SolveJob {
+    enum Phase { P_NONE, P_NORM, P_CYCLE, P_ITER, P_FINISH, P_DONE };
+    Hierarchy* h = nullptr;
+    nmg_solve_opts o{};
+    const double* b_user = nullptr;
+    double* x_user = nullptr;
+    bool b_dev = false, x_dev = false;
+    Phase phase = P_NONE;
+    int j = 0, its = 0, cycles = 0, engine = NMG_ENGINE_KERNELS;
+    double bnorm = 0.0, relres = 0.0;
+    nmg_status st = NMG_OK;
+    std::string err;
+    int64_t launches0 = 0, launches = 0;
+    std::chrono::steady_clock::time_point t0;
+};
+
+// ---------------------------------------------------------------------------
+// One FGMRES solve as a resumable job: job_enqueue() puts the next step on the
+// hierarchy's stream, job_advance() runs on the host once that work has
+// completed (it reads the few scalars copied back to pinned memory) and picks
+// the next step.  nmg_solve drives one job synchronously; the server drives
+// many jobs on different streams at once.
+// ---------------------------------------------------------------------------
+static void job_fail(SolveJob& J, nmg_status st) {
+    J.st = st;
+    J.err = g_last_error;
+}
+
+#define JOB_CK(call)                                                                 \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            fail(NMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+            job_fail(J, NMG_ERR_CUDA);                                               \
+            J.phase = SolveJob::P_DONE;                                              \
+            return;                                                                  \
+        }                                                                            \
+    } while (0)
+
+static void job_enqueue_cycle(SolveJob& J) {
+    Hierarchy* h = J.h;
     const Geom& g = h->lev[h->L - 1].g;
     const int64_t n = g.nodes * g.nc;
-    const int m = o.restart;
     cudaStream_t s = h->stream;
-    double* A64 = h->lev[h->L - 1].A64;
-    const bool b_dev = is_device_ptr(b_user), x_dev = is_device_ptr(x_user);
-    NMG_CK(cudaMemcpyAsync(h->b64, b_user, n * sizeof(double), b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    // true residual r = b - A x and beta = ||r||, v_0 = r / beta
+    launch_spmv<double>(g, h->lev[h->L - 1].A64, h->x64, h->b64, h->w64, true, s);
+    launch_norm2(h->w64, n, h->partial, h->scal + S_BETA, s);
+    launch_start_cycle(h->scal, J.o.restart, s);
+    launch_scale(h->w64, h->scal + S_INVH, false, h->V, n, s);
+    JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    J.phase = SolveJob::P_CYCLE;
+}
+
+static void job_enqueue_iter(SolveJob& J) {
+    Hierarchy* h = J.h;
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    const int j = J.j, m = J.o.restart;
+    cudaStream_t s = h->stream;
+    double* vj = h->V + (int64_t)j * n;
+    double* zj = h->Z + (int64_t)j * n;
+    const nmg_status st = precondition(h, J.o, vj, zj);
+    if (st != NMG_OK) {
+        job_fail(J, st);
+        J.phase = SolveJob::P_DONE;
+        return;
+    }
+    launch_spmv<double>(g, h->lev[h->L - 1].A64, zj, nullptr, h->w64, false, s);
+    // classical Gram-Schmidt, two passes
+    launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_HC, false, s);
+    launch_gs_update(h->V, n, j + 1, h->scal + S_HC, h->w64, n, h->partial, nullptr, false, s);
+    launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_Y, false, s);
+    launch_gs_update(h->V, n, j + 1, h->scal + S_Y, h->w64, n, h->partial, h->scal + S_HC + j + 1, true, s);
+    launch_arnoldi_finish(h->scal, j, m, s);
+    launch_scale(h->w64, h->scal + S_INVH, false, h->V + (int64_t)(j + 1) * n, n, s);
+    JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    J.phase = SolveJob::P_ITER;
+}
+
+static void job_enqueue_finish(SolveJob& J) {
+    Hierarchy* h = J.h;
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    cudaStream_t s = h->stream;
+    JOB_CK(cudaMemcpyAsync(J.x_user, h->x64, n * sizeof(double),
+                           J.x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    JOB_CK(wait_timeout_enqueue_read(h->host_flags + FLAG_COUNT, s));
+    JOB_CK(cudaMemcpyAsync(h->host_flags, h->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    J.phase = SolveJob::P_FINISH;
+}
+
+// Starts a job: validates, enqueues the copy of b and the norm of b.
+static nmg_status job_start(SolveJob& J, Hierarchy* h, const double* b_user, double* x_user,
+                            const nmg_solve_opts& o) {
+    J = SolveJob();
+    J.h = h;
+    J.o = o;
+    J.b_user = b_user;
+    J.x_user = x_user;
+    J.t0 = std::chrono::steady_clock::now();
+    J.launches0 = g_launches;
+    NMG_TRY(check_ready(h, o.precision));
+    NMG_TRY(ensure_krylov(h, o.restart));
+    NMG_TRY(resolve_engine(h, o, &J.engine));
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    cudaStream_t s = h->stream;
+    J.b_dev = is_device_ptr(b_user);
+    J.x_dev = is_device_ptr(x_user);
+    NMG_CK(cudaMemcpyAsync(h->b64, b_user, n * sizeof(double), J.b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     NMG_CK(cudaMemsetAsync(h->scal, 0, 8 * sizeof(double), s));
     NMG_CK(cudaMemsetAsync(h->x64, 0, n * sizeof(double), s));
     launch_norm2(h->b64, n, h->partial, h->scal + S_BNORM, s);
     NMG_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    NMG_CK(cudaStreamSynchronize(s));
-    const double bnorm = h->host_scal[S_BNORM];
-    nmg_status st = NMG_OK;
-    int its = 0, cycles = 0;
-    double relres = 0.0;
-    if (!std::isfinite(bnorm)) st = fail(NMG_ERR_NONFINITE, "non-finite right-hand side");
-    while (st == NMG_OK && bnorm > 0.0) {
-        // true residual r = b - A x and beta = ||r||
-        launch_spmv<double>(g, A64, h->x64, h->b64, h->w64, true, s);
-        launch_norm2(h->w64, n, h->partial, h->scal + S_BETA, s);
-        launch_start_cycle(h->scal, m, s);
-        launch_scale(h->w64, h->scal + S_INVH, false, h->V, n, s);
-        NMG_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        NMG_CK(cudaStreamSynchronize(s));
-        const double beta = h->host_scal[S_BETA];
-        relres = beta / bnorm;
-        if (!std::isfinite(beta)) { st = fail(NMG_ERR_NONFINITE, "non-finite residual"); break; }
-        if (relres <= o.rtol) break;
-        if (its >= o.maxit) { st = fail(NMG_ERR_NOT_CONVERGED, "maxit reached"); break; }
-        int k = 0;
-        for (int j = 0; j < m; ++j) {
-            double* vj = h->V + (int64_t)j * n;
-            double* zj = h->Z + (int64_t)j * n;
-            NMG_TRY(precondition(h, o, vj, zj));
-            launch_spmv<double>(g, A64, zj, nullptr, h->w64, false, s);
-            // classical Gram-Schmidt, two passes
-            launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_HC, false, s);
-            launch_gs_update(h->V, n, j + 1, h->scal + S_HC, h->w64, n, h->partial, nullptr, false, s);
-            launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_Y, false, s);
-            launch_gs_update(h->V, n, j + 1, h->scal + S_Y, h->w64, n, h->partial, h->scal + S_HC + j + 1, true, s);
-            launch_arnoldi_finish(h->scal, j, m, s);
-            launch_scale(h->w64, h->scal + S_INVH, false, h->V + (int64_t)(j + 1) * n, n, s);
-            NMG_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            NMG_CK(cudaStreamSynchronize(s));
-            ++its;
-            k = j + 1;
-            if (h->host_scal[S_STATUS] != 0.0) { st = fail(NMG_ERR_NONFINITE, "non-finite value in the Arnoldi process"); break; }
-            if (h->host_scal[S_EST] <= o.rtol || its >= o.maxit || h->host_scal[S_INVH] == 0.0) break;
+    J.launches = g_launches - J.launches0;
+    J.phase = SolveJob::P_NORM;
+    return NMG_OK;
+}
+
+// Host step after the enqueued work has completed.
+static void job_advance(SolveJob& J) {
+    Hierarchy* h = J.h;
+    const double* hs = h->host_scal;
+    switch (J.phase) {
+    case SolveJob::P_NORM:
+        J.bnorm = hs[S_BNORM];
+        if (!std::isfinite(J.bnorm)) {
+            fail(NMG_ERR_NONFINITE, "non-finite right-hand side");
+            job_fail(J, NMG_ERR_NONFINITE);
+            job_enqueue_finish(J);
+        } else if (J.bnorm == 0.0) {
+            job_enqueue_finish(J);
+        } else {
+            job_enqueue_cycle(J);
         }
-        if (st != NMG_OK) break;
-        launch_solve_update(h->scal, k, m, h->Z, n, h->x64, n, s);
-        ++cycles;
+        break;
+    case SolveJob::P_CYCLE: {
+        const double beta = hs[S_BETA];
+        J.relres = beta / J.bnorm;
+        if (!std::isfinite(beta)) {
+            fail(NMG_ERR_NONFINITE, "non-finite residual");
+            job_fail(J, NMG_ERR_NONFINITE);
+            job_enqueue_finish(J);
+        } else if (J.relres <= J.o.rtol) {
+            job_enqueue_finish(J);
+        } else if (J.its >= J.o.maxit) {
+            fail(NMG_ERR_NOT_CONVERGED, "maxit reached");
+            job_fail(J, NMG_ERR_NOT_CONVERGED);
+            job_enqueue_finish(J);
+        } else {
+            J.j = 0;
+            job_enqueue_iter(J);
+        }
+        break;
     }
-    NMG_CK(cudaMemcpyAsync(x_user, h->x64, n * sizeof(double), x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    NMG_CK(cudaStreamSynchronize(s));
+    case SolveJob::P_ITER: {
+        ++J.its;
+        const int k = J.j + 1;
+        if (hs[S_STATUS] != 0.0) {
+            fail(NMG_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+            job_fail(J, NMG_ERR_NONFINITE);
+            job_enqueue_finish(J);
+        } else if (hs[S_EST] <= J.o.rtol || J.its >= J.o.maxit || hs[S_INVH] == 0.0 || k == J.o.restart) {
+            const Geom& g = h->lev[h->L - 1].g;
+            const int64_t n = g.nodes * g.nc;
+            launch_solve_update(h->scal, k, J.o.restart, h->Z, n, h->x64, n, h->stream);
+            ++J.cycles;
+            job_enqueue_cycle(J);
+        } else {
+            J.j = k;
+            job_enqueue_iter(J);
+        }
+        break;
+    }
+    case SolveJob::P_FINISH: {
+        const int* f = h->host_flags;
+        if (f[FLAG_COUNT]) {
+            wait_timeout_clear(h->stream);
+            if (J.st == NMG_OK) {
+                fail(NMG_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy)");
+                job_fail(J, NMG_ERR_TIMEOUT);
+            }
+        }
+        if (f[FLAG_ABORT]) {
+            cudaMemsetAsync(h->flags + FLAG_ABORT, 0, sizeof(int), h->stream);
+            if (J.st == NMG_OK) {
+                fail(NMG_ERR_TIMEOUT, "the persistent V-cycle aborted (grid barrier or copy wait ran out)");
+                job_fail(J, NMG_ERR_TIMEOUT);
+            }
+        }
+        J.phase = SolveJob::P_DONE;
+        break;
+    }
+    default:
+        J.phase = SolveJob::P_DONE;
+        break;
+    }
+}
+
+static void job_info(const SolveJob& J, nmg_solve_info* info) {
+    if (!info) return;
+    info->iterations = J.its;
+    info->restarts = J.cycles > 0 ? J.cycles - 1 : 0;
+    info->rel_residual = J.relres;
+    info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - J.t0).count();
+    info->status = J.st;
+    info->launches = J.launches;
+    info->engine = J.engine;
+}
+
+static nmg_status solve_impl(Hierarchy* h, const double* b_user, double* x_user, const nmg_solve_opts& o,
+                             nmg_solve_info* info) {
+    SolveJob J;
+    NMG_TRY(job_start(J, h, b_user, x_user, o));
+    while (J.phase != SolveJob::P_DONE) {
+        NMG_CK(cudaStreamSynchronize(h->stream));
+        const int64_t l0 = g_launches;
+        job_advance(J);
+        J.launches += g_launches - l0;
+    }
     NMG_CK(cudaGetLastError());
-    if (info) {
-        info->iterations = its;
-        info->restarts = cycles > 0 ? cycles - 1 : 0;
-        info->rel_residual = relres;
-        info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        info->status = st;
-        info->launches = g_launches - launches0;
-    }
-    return st;
+    if (J.st != NMG_OK) g_last_error = J.err;
+    job_info(J, info);
+    return J.st;
 }
 
 }  // namespace nmg
@@ -373,6 +618,7 @@ nmg_status nmg_default_opts(nmg_solve_opts* o) {
     o->precision = NMG_PREC_FP32;
     o->weighting = NMG_WEIGHT_AVERAGE;
     o->use_graph = 1;
+    o->engine = NMG_ENGINE_AUTO;
     return NMG_OK;
 }
 
@@ -382,6 +628,7 @@ static void free_all(Hierarchy* h) {
     for (void* a : h->allocs) cudaFree(a);
     h->allocs.clear();
     if (h->host_scal) cudaFreeHost(h->host_scal);
+    if (h->host_flags) cudaFreeHost(h->host_flags);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     if (h->desc.stream == nullptr && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -479,8 +726,10 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if ((st = dalloc(h, (void**)&h->partial, (size_t)(kMaxRestart + 2) * kDotBlocks * sizeof(double))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->scal, S_COUNT * sizeof(double))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->flags, FLAG_COUNT * sizeof(int))) != NMG_OK) return cleanup(st);
+    if ((st = dalloc(h, (void**)&h->pbar, 2 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
     if (cudaMemset(h->flags, 0, FLAG_COUNT * sizeof(int)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
-    if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess)
+    if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess)
         return cleanup(fail(NMG_ERR_OOM, "pinned host allocation failed"));
     *out = h;
     return NMG_OK;
@@ -590,6 +839,9 @@ static nmg_status op_check(Hierarchy* h, int level, int prec, bool need_smooth) 
 static nmg_status finish_op(Hierarchy* h) {
     NMG_CK(cudaGetLastError());
     NMG_CK(cudaStreamSynchronize(h->stream));
+    int timed_out = 0;
+    NMG_CK(wait_timeout_flag(&timed_out, h->stream));
+    if (timed_out) return fail(NMG_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy)");
     return NMG_OK;
 }
 
@@ -656,18 +908,15 @@ nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* 
     NMG_TRY(validate_opts(opts));
     NMG_TRY(check_ready(h, opts->precision));
     enter(h);
-    const int prec = opts->precision;
-    Level& F = h->lev[h->L - 1];
-    const int64_t n = F.g.nodes * F.g.nc;
-    const size_t es = prec_size(prec);
-    if (opts->use_graph) {
-        NMG_CK(cudaMemcpyAsync(F.p[prec].b, r, n * es, cudaMemcpyDeviceToDevice, h->stream));
-        NMG_TRY(vcycle_graph(h, prec, *opts));
-        NMG_CK(cudaMemcpyAsync(z, F.p[prec].x, n * es, cudaMemcpyDeviceToDevice, h->stream));
-    } else {
-        vcycle_dispatch(h, prec, *opts, r, z);
+    NMG_TRY(vcycle_any(h, *opts, r, z, false));
+    NMG_TRY(finish_op(h));
+    int f[FLAG_COUNT];
+    NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f[FLAG_ABORT]) {
+        cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int));
+        return fail(NMG_ERR_TIMEOUT, "the persistent V-cycle aborted (grid barrier or copy wait ran out)");
     }
-    return finish_op(h);
+    return NMG_OK;
 }
 
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int prec, int64_t first, int64_t count, double* out) {
@@ -726,6 +975,221 @@ nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launche
     // algorithmic bytes of one finest-level Vanka apply: every patch inverse once,
     // the residual once and the per-patch corrections written once
     if (bytes_per_launch) *bytes_per_launch = h->prof_bytes;
+    return NMG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of solves on resident hierarchies.
+//
+// A worker thread owns all CUDA calls of the server.  Submitted requests wait
+// in a FIFO; a request is admitted when a slot is free, its hierarchy is not
+// running another request (a hierarchy's workspace serves one solve at a
+// time) and the resident bytes of the hierarchies with running requests stay
+// within the memory budget.  Running requests advance as resumable jobs on
+// their hierarchies' streams: the worker enqueues a step, records an event,
+// and moves a job on as soon as its event has completed, so the steps of
+// different requests overlap on the device.  Every step performs the same
+// kernels in the same order as nmg_solve, so a result does not depend on what
+// else runs beside it.
+// ---------------------------------------------------------------------------
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+
+namespace nmg {
+
+struct Request {
+    uint64_t ticket = 0;
+    Hierarchy* h = nullptr;
+    const double* b = nullptr;
+    double* x = nullptr;
+    nmg_solve_opts o{};
+    SolveJob job;
+    cudaEvent_t ev = nullptr;
+    bool done = false;
+    nmg_solve_info info{};
+    std::string err;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Server {
+    size_t budget = 0;
+    int max_slots = 1;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_done, cv_work;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, Request*> by_ticket;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+static void finish_request(Server* S, Request* r, std::vector<Request*>& active, std::unordered_set<Hierarchy*>& busy,
+                           size_t& active_bytes) {
+    job_info(r->job, &r->info);
+    r->info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count();
+    r->err = r->job.err;
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+    busy.erase(r->h);
+    active_bytes -= r->h->bytes;
+    active.erase(std::find(active.begin(), active.end(), r));
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->done = true;
+    S->cv_done.notify_all();
+}
+
+static void server_loop(Server* S) {
+    cudaSetDevice(S->device);
+    std::vector<Request*> active;
+    std::unordered_set<Hierarchy*> busy;
+    size_t active_bytes = 0;
+    for (;;) {
+        std::vector<Request*> admit;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (active.empty() && S->queue.empty()) {
+                if (S->stop) break;
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+            for (auto it = S->queue.begin(); it != S->queue.end() && (int)(active.size() + admit.size()) < S->max_slots;) {
+                Request* r = *it;
+                const bool fits = S->budget == 0 || active_bytes + r->h->bytes <= S->budget || active.empty();
+                if (!busy.count(r->h) && fits) {
+                    busy.insert(r->h);
+                    active_bytes += r->h->bytes;
+                    admit.push_back(r);
+                    it = S->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (Request* r : admit) {
+            active.push_back(r);
+            const int64_t l0 = g_launches;
+            nmg_status st = job_start(r->job, r->h, r->b, r->x, r->o);
+            if (st == NMG_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(r->ev, r->h->stream);
+            } else {
+                if (st == NMG_OK) st = fail(NMG_ERR_CUDA, "event creation failed");
+                r->job.st = st;
+                r->job.err = g_last_error;
+                r->job.phase = SolveJob::P_DONE;
+            }
+            r->job.launches = g_launches - l0;
+        }
+        bool progressed = !admit.empty();
+        for (size_t i = 0; i < active.size();) {
+            Request* r = active[i];
+            if (r->job.phase != SolveJob::P_DONE) {
+                const cudaError_t q = cudaEventQuery(r->ev);
+                if (q == cudaErrorNotReady) { ++i; continue; }
+                progressed = true;
+                if (q != cudaSuccess) {
+                    fail(NMG_ERR_CUDA, std::string("request failed: ") + cudaGetErrorString(q));
+                    r->job.st = NMG_ERR_CUDA;
+                    r->job.err = g_last_error;
+                    r->job.phase = SolveJob::P_DONE;
+                } else {
+                    const int64_t l0 = g_launches;
+                    job_advance(r->job);
+                    r->job.launches += g_launches - l0;
+                    if (r->job.phase != SolveJob::P_DONE) cudaEventRecord(r->ev, r->h->stream);
+                }
+            }
+            if (r->job.phase == SolveJob::P_DONE) {
+                cudaStreamSynchronize(r->h->stream);
+                finish_request(S, r, active, busy, active_bytes);
+                progressed = true;
+                continue;
+            }
+            ++i;
+        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+}
+
+}  // namespace nmg
+
+extern "C" {
+
+nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server** out) {
+    if (!out || max_slots < 1 || max_slots > 1024) return fail(NMG_ERR_INVALID, "bad server arguments");
+    auto* S = new nmg::Server();
+    S->budget = mem_budget_bytes;
+    S->max_slots = max_slots;
+    cudaGetDevice(&S->device);
+    S->worker = std::thread(nmg::server_loop, S);
+    *out = reinterpret_cast<nmg_server*>(S);
+    return NMG_OK;
+}
+
+nmg_status nmg_submit(nmg_server* server, nmg_hierarchy* h, const double* b, double* x, const nmg_solve_opts* opts,
+                      uint64_t* ticket) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S || !h || !b || !x || !ticket) return fail(NMG_ERR_INVALID, "NULL argument");
+    NMG_TRY(validate_opts(opts));
+    if (S->budget && h->bytes > S->budget)
+        return fail(NMG_ERR_OOM, "hierarchy larger than the server's memory budget");
+    auto* r = new nmg::Request();
+    r->h = h;
+    r->b = b;
+    r->x = x;
+    r->o = *opts;
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete r;
+            return fail(NMG_ERR_INVALID, "server is shutting down");
+        }
+        r->ticket = S->next_ticket++;
+        S->by_ticket[r->ticket] = r;
+        S->queue.push_back(r);
+    }
+    S->cv_work.notify_one();
+    *ticket = r->ticket;
+    return NMG_OK;
+}
+
+nmg_status nmg_poll(nmg_server* server, uint64_t ticket, int timeout_ms, nmg_solve_info* info) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S) return fail(NMG_ERR_INVALID, "NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->by_ticket.find(ticket);
+    if (it == S->by_ticket.end()) return fail(NMG_ERR_INVALID, "unknown ticket");
+    nmg::Request* r = it->second;
+    if (!r->done) {
+        if (timeout_ms <= 0) return NMG_PENDING;
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; });
+        if (!r->done) return fail(NMG_ERR_TIMEOUT, "request still running at the poll deadline");
+    }
+    if (info) *info = r->info;
+    const nmg_status st = r->info.status;
+    if (st != NMG_OK) g_last_error = r->err;
+    S->by_ticket.erase(it);
+    delete r;
+    return st;
+}
+
+nmg_status nmg_server_destroy(nmg_server* server) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S) return NMG_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (auto& kv : S->by_ticket) delete kv.second;
+    delete S;
     return NMG_OK;
 }
 

@@ -1,0 +1,256 @@
+// Per-element device functions of the V-cycle, shared by the one-kernel-per-
+// step path (smooth_kernels.cu) and the persistent V-cycle (persistent.cu), so
+// both paths perform the same arithmetic in the same order.
+#pragma once
+
+#include "nmg_internal.cuh"
+
+namespace nmg {
+namespace elem {
+
+template <typename T, typename TS> struct Cvt;
+template <> struct Cvt<double, double> { static __device__ __forceinline__ double f(double v) { return v; } };
+template <> struct Cvt<float, float> { static __device__ __forceinline__ float f(float v) { return v; } };
+template <> struct Cvt<float, __nv_bfloat16> {
+    static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+
+template <typename TS> __device__ __forceinline__ TS ldg(const TS* p) { return __ldg(p); }
+template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) { return *p; }
+
+__device__ __forceinline__ void node_xyz(const Geom& g, int64_t i, int& x, int& y, int& z) {
+    x = (int)(i % g.nn[0]);
+    int64_t t = i / g.nn[0];
+    y = (int)(t % g.nn[1]);
+    z = (int)(t / g.nn[1]);
+}
+
+__device__ __forceinline__ void patch_xyz(const Geom& g, int64_t p, int& px, int& py, int& pz) {
+    px = (int)(p % g.pc[0]);
+    py = (int)((p / g.pc[0]) % g.pc[1]);
+    pz = (int)(p / ((int64_t)g.pc[0] * g.pc[1]));
+}
+
+__device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int pz, int an) {
+    const int ax = an % 3, ay = (an / 3) % 3, az = an / 9;
+    return (int64_t)(2 * px + ax) + (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
+}
+
+// y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout).
+template <typename T, int DIM>
+__device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
+                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
+    constexpr int NC = DIM + 1;
+    constexpr int NB = NC * NC;
+    constexpr int NST = (DIM == 2) ? 9 : 27;
+    int ix, iy, iz;
+    node_xyz(g, i, ix, iy, iz);
+    const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
+    T acc[NC];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) acc[r] = T(0);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+        const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                        (iz + dz >= 0) && (iz + dz < g.nn[2]);
+        if (ok) {
+            const int64_t j = i + dx + dy * sy + dz * sz;
+            T xv[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) xv[c] = x[j * NC + c];
+            const T* As = A + (int64_t)s * NB * g.ld + i;
+#pragma unroll
+            for (int r = 0; r < NC; ++r)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[r] = fma(__ldg(As + (int64_t)(r * NC + c) * g.ld), xv[c], acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r) y[i * NC + r] = residual ? b[i * NC + r] - acc[r] : acc[r];
+}
+
+// Gathers R_p d into sd[0..NP) (called by one warp; lane-strided).
+template <typename T, int DIM>
+__device__ __forceinline__ void gather_patch(const Geom& g, const T* __restrict__ d, int64_t p, T* sd, int lane) {
+    constexpr int NC = DIM + 1;
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
+    int px, py, pz;
+    patch_xyz(g, p, px, py, pz);
+    for (int t = lane; t < NP; t += 32) {
+        const int an = t / NC, c = t - an * NC;
+        sd[t] = d[patch_node(g, px, py, pz, an) * NC + c];
+    }
+}
+
+// corr_p = A_p^{-1} sd for one patch by one warp (lane owns rows lane + 32 q);
+// Ap: column-major inverse (global or shared memory).
+template <typename T, typename TS, int DIM, bool GLOBAL>
+__device__ __forceinline__ void apply_patch(const TS* Ap, const T* sd, T* __restrict__ corr_p, int lane) {
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * (DIM + 1);
+    constexpr int NQ = (NP + 31) / 32;
+    T acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = T(0);
+#pragma unroll 4
+    for (int j = 0; j < NP; ++j) {
+        const T dj = sd[j];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int row = lane + 32 * q;
+            if (row < NP) {
+                const TS a = GLOBAL ? ldg(Ap + j * NP + row) : Ap[j * NP + row];
+                acc[q] = fma(Cvt<T, TS>::f(a), dj, acc[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int row = lane + 32 * q;
+        if (row < NP) corr_p[row] = acc[q];
+    }
+}
+
+// x_i += w_i * (sum of the corrections of the patches containing node i), in
+// ascending patch order; w_i = omega / multiplicity ("average") or omega.
+template <typename T, int DIM>
+__device__ __forceinline__ void vanka_update_node(const Geom& g, const T* __restrict__ corr, T* __restrict__ x,
+                                                  bool x_zero, T omega, bool average, int64_t i) {
+    constexpr int NC = DIM + 1;
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
+    int xyz[3];
+    node_xyz(g, i, xyz[0], xyz[1], xyz[2]);
+    int cp[3][2], cl[3][2], cnt[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int c = xyz[k];
+        if (k >= DIM) { cp[k][0] = 0; cl[k][0] = 0; cnt[k] = 1; continue; }
+        if (c & 1) { cp[k][0] = (c - 1) >> 1; cl[k][0] = 1; cnt[k] = 1; }
+        else {
+            int n = 0;
+            if (c > 0) { cp[k][n] = (c >> 1) - 1; cl[k][n] = 2; ++n; }
+            if (c < g.cells[k]) { cp[k][n] = c >> 1; cl[k][n] = 0; ++n; }
+            cnt[k] = n;
+        }
+    }
+    T sum[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sum[c] = T(0);
+    for (int a = 0; a < cnt[2]; ++a)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int e = 0; e < cnt[0]; ++e) {
+                const int64_t p = cp[0][e] + (int64_t)g.pc[0] * (cp[1][b] + (int64_t)g.pc[1] * cp[2][a]);
+                const int loc = cl[0][e] + 3 * cl[1][b] + 9 * cl[2][a];
+                const T* cpn = corr + p * NP + loc * NC;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sum[c] += cpn[c];
+            }
+    const int m = cnt[0] * cnt[1] * cnt[2];
+    const T wgt = average ? omega / T(m) : omega;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const T old = x_zero ? T(0) : x[i * NC + c];
+        x[i * NC + c] = old + wgt * sum[c];
+    }
+}
+
+// (r_c)_I = (P^T r_f)_I, zero on coarse Dirichlet entries.
+template <typename T, int DIM>
+__device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, const T* __restrict__ rf,
+                                              T* __restrict__ rc, const uint8_t* __restrict__ cmask, int64_t I) {
+    constexpr int NC = DIM + 1;
+    int X, Y, Z;
+    node_xyz(c, I, X, Y, Z);
+    T sum[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) sum[k] = T(0);
+    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+    for (int oz = zlo; oz <= zhi; ++oz) {
+        const int fz = 2 * Z + oz;
+        if (fz < 0 || fz >= f.nn[2]) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int fy = 2 * Y + oy;
+            if (fy < 0 || fy >= f.nn[1]) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int fx = 2 * X + ox;
+                if (fx < 0 || fx >= f.nn[0]) continue;
+                const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+                const int64_t fi = fx + (int64_t)f.nn[0] * (fy + (int64_t)f.nn[1] * fz);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) sum[k] = fma(w, rf[fi * NC + k], sum[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rc[I * NC + k] = cmask[I * NC + k] ? T(0) : sum[k];
+}
+
+// (x_f)_i += (P e_c)_i, fine Dirichlet entries untouched.
+template <typename T, int DIM>
+__device__ __forceinline__ void prolong_node(const Geom& f, const Geom& c, const T* __restrict__ ec,
+                                             T* __restrict__ xf, const uint8_t* __restrict__ fmask, int64_t i) {
+    constexpr int NC = DIM + 1;
+    int xyz[3];
+    node_xyz(f, i, xyz[0], xyz[1], xyz[2]);
+    int ci[3][2], cnt[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int v = xyz[k];
+        if (k >= DIM || !(v & 1)) { ci[k][0] = v >> 1; cnt[k] = 1; }
+        else { ci[k][0] = (v - 1) >> 1; ci[k][1] = (v + 1) >> 1; cnt[k] = 2; }
+    }
+    T sum[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) sum[k] = T(0);
+    for (int a = 0; a < cnt[2]; ++a)
+        for (int b = 0; b < cnt[1]; ++b)
+            for (int e = 0; e < cnt[0]; ++e) {
+                const T w = (cnt[0] == 2 ? T(0.5) : T(1)) * (cnt[1] == 2 ? T(0.5) : T(1)) *
+                            (cnt[2] == 2 ? T(0.5) : T(1));
+                const int64_t I = ci[0][e] + (int64_t)c.nn[0] * (ci[1][b] + (int64_t)c.nn[1] * ci[2][a]);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) sum[k] = fma(w, ec[I * NC + k], sum[k]);
+            }
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+        if (!fmask[i * NC + k]) xf[i * NC + k] += sum[k];
+}
+
+// x_row = (inv b)_row with FP64 sums, by one warp.
+template <typename T>
+__device__ __forceinline__ void coarse_row(const double* __restrict__ inv, int64_t n, const T* __restrict__ b,
+                                           T* __restrict__ x, int64_t row, int lane) {
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s = fma(inv[row * n + j], (double)b[j], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) x[row] = (T)s;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One TMA bulk copy of `bytes` (multiple of 16, 16-byte aligned ends) completing on bar.
+__device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+}  // namespace elem
+}  // namespace nmg

@@ -28,6 +28,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __global__ void __launch_bounds__(kThreads)
 k_multidot_partial(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w,
                    int64_t n, double* __restrict__ partial) {
+    NMG_PDL_ENTRY();
     __shared__ double red[kThreads / 32];
     for (int kc = 0; kc < nvec; kc += kChunk) {
         double acc[kChunk];
@@ -51,6 +52,7 @@ k_multidot_partial(const double* __restrict__ V, int64_t ldv, int nvec, const do
 // out[k] (+)= sum_blk partial[k][blk], one warp per k, fixed order.
 __global__ void k_finish_dots(const double* __restrict__ partial, int nvec, double* out, bool accumulate,
                               bool take_sqrt) {
+    NMG_PDL_ENTRY();
     const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= nvec) return;
@@ -67,6 +69,7 @@ __global__ void k_finish_dots(const double* __restrict__ partial, int nvec, doub
 __global__ void __launch_bounds__(kThreads)
 k_gs_update(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
             double* __restrict__ w, int64_t n, double* __restrict__ partial, bool want_norm) {
+    NMG_PDL_ENTRY();
     __shared__ double red[kThreads / 32];
     __shared__ double hs[kMaxRestart + 1];
     for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
@@ -86,6 +89,7 @@ k_gs_update(const double* __restrict__ V, int64_t ldv, int nvec, const double* _
 
 __global__ void __launch_bounds__(kThreads)
 k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ partial) {
+    NMG_PDL_ENTRY();
     __shared__ double red[kThreads / 32];
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads)
@@ -98,6 +102,7 @@ k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ pa
 // ||w||): apply the earlier rotations, build rotation j, update g, write the
 // residual estimate |g_{j+1}| / ||b|| and 1 / h_{j+1,j}.
 __global__ void k_arnoldi_finish(double* scal, int j, int m) {
+    NMG_PDL_ENTRY();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double* H = scal + S_H + (int64_t)j * (m + 1);
     const double* hc = scal + S_HC;
@@ -131,6 +136,7 @@ __global__ void k_arnoldi_finish(double* scal, int j, int m) {
 }
 
 __global__ void k_start_cycle(double* scal, int m) {
+    NMG_PDL_ENTRY();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     for (int i = 0; i <= m; ++i) scal[S_G + i] = 0.0;
     const double beta = scal[S_BETA];
@@ -140,6 +146,7 @@ __global__ void k_start_cycle(double* scal, int m) {
 }
 
 __global__ void k_scale(const double* __restrict__ x, const double* __restrict__ sp, double* __restrict__ y, int64_t n) {
+    NMG_PDL_ENTRY();
     const double a = *sp;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i];
@@ -147,6 +154,7 @@ __global__ void k_scale(const double* __restrict__ x, const double* __restrict__
 
 // y = H[:k,:k]^{-1} g[:k] by back substitution (single thread).
 __global__ void k_backsolve(double* scal, int k, int m) {
+    NMG_PDL_ENTRY();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double* H = scal + S_H;
     double* y = scal + S_Y;
@@ -161,6 +169,7 @@ __global__ void k_backsolve(double* scal, int k, int m) {
 __global__ void __launch_bounds__(kThreads)
 k_update_x(const double* __restrict__ scal, int k, const double* __restrict__ Z, int64_t ldz,
            double* __restrict__ x, int64_t n) {
+    NMG_PDL_ENTRY();
     __shared__ double ys[kMaxRestart];
     for (int i = threadIdx.x; i < k; i += kThreads) ys[i] = scal[S_Y + i];
     __syncthreads();
@@ -172,6 +181,7 @@ k_update_x(const double* __restrict__ scal, int k, const double* __restrict__ Z,
 }
 
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
+    NMG_PDL_ENTRY();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
 }
@@ -186,44 +196,44 @@ inline unsigned grid_for(int64_t n) {
 
 void launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t s) {
     g_launches += 2;
-    k_sumsq_partial<<<kDotBlocks, kThreads, 0, s>>>(x, n, partial);
-    k_finish_dots<<<1, 32, 0, s>>>(partial, 1, out, false, true);
+    pdl_launch(k_sumsq_partial, dim3(kDotBlocks), dim3(kThreads), 0, s, x, n, partial);
+    pdl_launch(k_finish_dots, dim3(1), dim3(32), 0, s, partial, 1, out, false, true);
 }
 
 void launch_multidot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
                      double* out, bool accumulate, cudaStream_t s) {
     g_launches += 2;
-    k_multidot_partial<<<kDotBlocks, kThreads, 0, s>>>(V, ldv, nvec, w, n, partial);
-    k_finish_dots<<<(nvec + 7) / 8, 256, 0, s>>>(partial, nvec, out, accumulate, false);
+    pdl_launch(k_multidot_partial, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, w, n, partial);
+    pdl_launch(k_finish_dots, dim3((nvec + 7) / 8), dim3(256), 0, s, partial, nvec, out, accumulate, false);
 }
 
 void launch_gs_update(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
                       double* partial, double* nrm2, bool want_norm, cudaStream_t s) {
     g_launches += want_norm ? 2 : 1;
-    k_gs_update<<<kDotBlocks, kThreads, 0, s>>>(V, ldv, nvec, h, w, n, partial, want_norm);
-    if (want_norm) k_finish_dots<<<1, 32, 0, s>>>(partial, 1, nrm2, false, true);
+    pdl_launch(k_gs_update, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, h, w, n, partial, want_norm);
+    if (want_norm) pdl_launch(k_finish_dots, dim3(1), dim3(32), 0, s, partial, 1, nrm2, false, true);
 }
 
-void launch_arnoldi_finish(double* scal, int j, int m, cudaStream_t s) { k_arnoldi_finish<<<1, 32, 0, s>>>(scal, j, m); }
+void launch_arnoldi_finish(double* scal, int j, int m, cudaStream_t s) { pdl_launch(k_arnoldi_finish, dim3(1), dim3(32), 0, s, scal, j, m); }
 
 void launch_scale(const double* x, const double* scal_ptr, bool invert, double* y, int64_t n, cudaStream_t s) {
     g_launches += 1;
     (void)invert;
-    k_scale<<<grid_for(n), 256, 0, s>>>(x, scal_ptr, y, n);
+    pdl_launch(k_scale, dim3(grid_for(n)), dim3(256), 0, s, x, scal_ptr, y, n);
 }
 
-void launch_start_cycle(double* scal, int m, cudaStream_t s) { k_start_cycle<<<1, 32, 0, s>>>(scal, m); }
+void launch_start_cycle(double* scal, int m, cudaStream_t s) { pdl_launch(k_start_cycle, dim3(1), dim3(32), 0, s, scal, m); }
 
 void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x, int64_t n,
                          cudaStream_t s) {
     g_launches += 2;
-    k_backsolve<<<1, 32, 0, s>>>(scal, k, m);
-    k_update_x<<<grid_for(n), kThreads, 0, s>>>(scal, k, Z, ldz, x, n);
+    pdl_launch(k_backsolve, dim3(1), dim3(32), 0, s, scal, k, m);
+    pdl_launch(k_update_x, dim3(grid_for(n)), dim3(kThreads), 0, s, scal, k, Z, ldz, x, n);
 }
 
 void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s) {
     g_launches += 1;
-    k_axpby<<<grid_for(n), 256, 0, s>>>(a, x, b, y, n);
+    pdl_launch(k_axpby, dim3(grid_for(n)), dim3(256), 0, s, a, x, b, y, n);
 }
 
 }  // namespace nmg

@@ -77,6 +77,7 @@ struct Hierarchy {
     double* partial = nullptr;    // kMaxRestart + 2 rows of kDotBlocks partial sums
     double* scal = nullptr;       // device scalars (see krylov kernels)
     double* host_scal = nullptr;  // pinned mirror of a few scalars
+    int* host_flags = nullptr;    // pinned mirror of the flags and the wait-timeout flag
     int* flags = nullptr;         // device error flags
     int m_alloc = 0;
     size_t bytes = 0;
@@ -92,12 +93,22 @@ struct Hierarchy {
     int64_t prof_launches = 0;
     int64_t launches = 0;               // kernels enqueued (graph nodes counted per replay)
     int64_t vgraph_nodes[3] = {0, 0, 0};
+    // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
+    unsigned* pbar = nullptr;
+    int engine_choice[3] = {0, 0, 0};
+    int engine_key[3][3] = {};
+    double engine_us[3][2] = {};
     double prof_bytes = 0.0;
     std::vector<void*> allocs;
 };
 
 // Error flags (device int array)
-enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_COUNT = 4 };
+enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_ABORT = 3, FLAG_COUNT = 4 };
+
+// Persistent V-cycle (persistent.cu) on the finest level's buffers of precision prec.
+struct Hierarchy;
+cudaError_t launch_vcycle_persistent(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting,
+                                     unsigned* bar, int* abort, int small_patches);
 
 // ---------------------------------------------------------------------------
 // Launchers (setup_kernels.cu)
@@ -167,4 +178,37 @@ namespace nmg {
 // Kernels enqueued by the calling thread (launchers add to it; a graph replay
 // adds the number of kernel nodes it holds).
 extern thread_local int64_t g_launches;
+
+// Programmatic dependent launch: every solve-phase kernel is launched with
+// programmatic stream serialisation, so its launch overlaps the drain of the
+// kernel before it.  A kernel waits for its predecessor's results with
+// NMG_PDL_WAIT() before touching memory and then lets its own successor launch.
+#define NMG_PDL_ENTRY()                                      \
+    do {                                                     \
+        asm volatile("griddepcontrol.wait;" ::: "memory");   \
+        asm volatile("griddepcontrol.launch_dependents;");   \
+    } while (0)
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Device flag raised by a bounded wait that ran out (a TMA copy that did not
+// complete); read and cleared by the host after a solve.
+cudaError_t wait_timeout_flag(int* value, cudaStream_t s);
+// Stream-ordered variants: enqueue a copy of the flag to (pinned) dst; clear it.
+cudaError_t wait_timeout_enqueue_read(int* dst, cudaStream_t s);
+cudaError_t wait_timeout_clear(cudaStream_t s);
 }  // namespace nmg

@@ -33,6 +33,10 @@ NMG_PREC_BF16 = 2
 NMG_WEIGHT_AVERAGE = 0
 NMG_WEIGHT_SUM = 1
 
+NMG_ENGINE_AUTO = 0
+NMG_ENGINE_KERNELS = 1
+NMG_ENGINE_PERSISTENT = 2
+
 
 class nmg_mesh_desc(C.Structure):
     _fields_ = [
@@ -59,6 +63,7 @@ class nmg_solve_opts(C.Structure):
         ("precision", C.c_int),
         ("weighting", C.c_int),
         ("use_graph", C.c_int),
+        ("engine", C.c_int),
     ]
 
 
@@ -70,6 +75,7 @@ class nmg_solve_info(C.Structure):
         ("ms_total", C.c_double),
         ("status", C.c_int),
         ("launches", C.c_int64),
+        ("engine", C.c_int),
     ]
 
 
@@ -102,6 +108,10 @@ _SIGS = {
     "nmg_destroy_hierarchy": [_H],
     "nmg_profile_enable": [_H, C.c_int],
     "nmg_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "nmg_server_create": [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)],
+    "nmg_submit": [C.c_void_p, _H, _P, _P, C.POINTER(nmg_solve_opts), C.POINTER(C.c_uint64)],
+    "nmg_poll": [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(nmg_solve_info)],
+    "nmg_server_destroy": [C.c_void_p],
     "nmg_vanka_correct_noalloc": [C.c_int, C.POINTER(C.c_int), C.c_int, _P, C.c_int64, _P, _P, C.c_double,
                                   C.c_int, C.c_int, _P],
 }
@@ -207,3 +217,19 @@ def nmg_vanka_correct_noalloc(dim, cells, precision, inv, inv_stride, d, x, omeg
     c = (C.c_int * 3)(*(list(cells) + [0] * (3 - len(cells))))
     return _lib.nmg_vanka_correct_noalloc(dim, c, precision, ptr(inv), inv_stride, ptr(d), ptr(x), omega,
                                           weighting, x_is_zero, stream)
+
+
+def nmg_server_create(mem_budget_bytes, max_slots, out: C.c_void_p) -> int:
+    return _lib.nmg_server_create(mem_budget_bytes, max_slots, C.byref(out))
+
+
+def nmg_submit(server, h, b, x, opts: nmg_solve_opts, ticket: C.c_uint64) -> int:
+    return _lib.nmg_submit(server, h, ptr(b), ptr(x), C.byref(opts), C.byref(ticket))
+
+
+def nmg_poll(server, ticket, timeout_ms, info: nmg_solve_info) -> int:
+    return _lib.nmg_poll(server, ticket, timeout_ms, C.byref(info) if info is not None else None)
+
+
+def nmg_server_destroy(server) -> int:
+    return _lib.nmg_server_destroy(server)

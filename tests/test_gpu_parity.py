@@ -189,15 +189,15 @@ def test_transfers_and_coarse(nmg, built, sessions, case, prec):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("use_graph", [0, 1])
-def test_vcycle(nmg, built, sessions, case, prec, use_graph):
+@pytest.mark.parametrize("engine,use_graph", [(1, 0), (1, 1), (2, 0)])
+def test_vcycle(nmg, built, sessions, case, prec, engine, use_graph):
     from paper_1904_02401_gb300.session import solve_opts
     s, h = built[case]
     S = sessions[case]
     dt = vdtype(prec)
     r = s.rhs.astype(dt).astype(np.float64)
     z = torch.zeros(r.size, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
-    nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=use_graph), cu(r, dt), z))
+    nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=use_graph, engine=engine), cu(r, dt), z))
     ref = h.vcycle(r)
     tol = 1e-8 if prec == 0 else (1e-3 if prec == 1 else 5e-2)
     assert rel(host(z), ref) < tol
@@ -305,3 +305,36 @@ def test_error_paths(nmg, built):
     S2 = Session(2, s.problem.n, lv, s.dirichlet, precisions=1 << 1)
     assert nmg.nmg_solve(S2.handle, b, x, solve_opts(precision=0), info) == nmg.NMG_ERR_INVALID
     S2.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", PRECS)
+def test_engines_agree(nmg, built, sessions, case, prec):
+    """One-kernel-per-step (plain and graph) and persistent V-cycles run the same
+    element code in the same order: their results are bitwise identical."""
+    from paper_1904_02401_gb300.session import solve_opts
+    s, h = built[case]
+    S = sessions[case]
+    dt = vdtype(prec)
+    r = cu(s.rhs.astype(dt), dt)
+    outs = []
+    for engine, graph in ((nmg.NMG_ENGINE_KERNELS, 0), (nmg.NMG_ENGINE_KERNELS, 1), (nmg.NMG_ENGINE_PERSISTENT, 0)):
+        z = torch.zeros_like(r)
+        nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=graph, engine=engine), r, z))
+        outs.append(z)
+    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_fp64_persistent_engine(nmg, built, sessions, case):
+    s, h = built[case]
+    S = sessions[case]
+    hist = []
+    xo, info_o = fgmres(h.fine.A.matvec, h.vcycle, s.rhs, rtol=1e-8, history=hist)
+    b = cu(s.rhs, np.float64)
+    x = torch.empty_like(b)
+    info = S.solve(b, x, precision=0, engine=nmg.NMG_ENGINE_PERSISTENT)
+    assert info.status == 0
+    assert _iteration_tie_ok(info.iterations, info_o["iterations"], hist, 1e-8)
+    assert rel(host(x), xo) <= 1e-8

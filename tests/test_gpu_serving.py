@@ -1,0 +1,132 @@
+"""Serving: continuous batching of solves on resident hierarchies (C ABI nmg_server_*).
+
+Each request's result must be the same alone (nmg_solve) and in a mix of
+concurrently running requests of different meshes; the kernels are
+deterministic, so the expected agreement is bitwise.
+"""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gen import Problem, build_system
+
+pytestmark = pytest.mark.gpu
+
+MESHES = [
+    Problem(dim=2, n=(32, 32), levels=3, solid=(0, +1, 0.6), conv_seed=10),
+    Problem(dim=2, n=(64, 64), levels=4, solid=(0, +1, 0.6), conv_seed=12),
+    Problem(dim=2, n=(24, 40), levels=3, solid=(0, +1, 0.6), conv_seed=14),
+    Problem(dim=3, n=(8, 8, 8), levels=2, solid=(2, -1, 0.25), conv_seed=16),
+    Problem(dim=3, n=(16, 16, 16), levels=3, solid=(2, -1, 0.25), conv_seed=18),
+]
+
+
+@pytest.fixture(scope="module")
+def pool():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_02401_gb300.session import Session
+    out = []
+    for p in MESHES:
+        s = build_system(p)
+        S = Session(p.dim, p.n, [(l.row_ptr, l.col_idx, l.vals) for l in s.levels], s.dirichlet,
+                    precisions=(1 << 0) | (1 << 1))
+        out.append((s, S))
+    yield out
+    for _, S in out:
+        S.close()
+
+
+def _rhs(s, seed):
+    rng = np.random.default_rng(seed)
+    b = rng.uniform(-1.0, 1.0, s.unknowns)
+    b[s.dirichlet.astype(bool)] = 0.0
+    return torch.from_numpy(b).cuda()
+
+
+def test_results_identical_alone_and_in_the_mix(pool):
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    reqs = []
+    for i in range(20):
+        k = i % len(pool)
+        prec = (1, 0)[i % 2]
+        reqs.append((k, prec, 100 + i))
+    # alone
+    alone = []
+    for k, prec, seed in reqs:
+        s, S = pool[k]
+        b = _rhs(s, seed)
+        x = torch.empty_like(b)
+        info = S.solve(b, x, precision=prec, engine=nmg.NMG_ENGINE_KERNELS)
+        assert info.status == 0
+        alone.append((x.clone(), info.iterations))
+    # in the mix
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(0, 4, server))
+    try:
+        bufs, tickets = [], []
+        for k, prec, seed in reqs:
+            s, S = pool[k]
+            b = _rhs(s, seed)
+            x = torch.zeros_like(b)
+            bufs.append((b, x))
+        torch.cuda.synchronize()
+        for (k, prec, seed), (b, x) in zip(reqs, bufs):
+            t = C.c_uint64()
+            nmg.check(nmg.nmg_submit(server, pool[k][1].handle, b, x,
+                                     solve_opts(precision=prec, engine=nmg.NMG_ENGINE_KERNELS), t))
+            tickets.append(t.value)
+        for i, t in enumerate(tickets):
+            info = nmg.nmg_solve_info()
+            st = nmg.nmg_poll(server, t, 60000, info)
+            assert st == 0, (st, nmg.nmg_last_error())
+            x = bufs[i][1]
+            assert torch.equal(x, alone[i][0]), i
+            assert info.iterations == alone[i][1]
+            assert info.ms_total > 0
+        # a released ticket is unknown afterwards
+        assert nmg.nmg_poll(server, tickets[0], 0, None) == nmg.NMG_ERR_INVALID
+    finally:
+        nmg.nmg_server_destroy(server)
+
+
+def test_memory_budget_admission(pool):
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    sizes = [S.bytes() for _, S in pool]
+    # budget fits the largest hierarchy alone: requests still all complete (one at a time when needed)
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(max(sizes), 8, server))
+    try:
+        bufs, tickets = [], []
+        for i, (s, S) in enumerate(pool):
+            b = _rhs(s, 7 + i)
+            x = torch.zeros_like(b)
+            bufs.append((b, x, s, S))
+        torch.cuda.synchronize()
+        for b, x, s, S in bufs:
+            t = C.c_uint64()
+            nmg.check(nmg.nmg_submit(server, S.handle, b, x, solve_opts(precision=1), t))
+            tickets.append(t.value)
+        for t, (b, x, s, S) in zip(tickets, bufs):
+            info = nmg.nmg_solve_info()
+            assert nmg.nmg_poll(server, t, 60000, info) == 0
+            assert info.rel_residual <= 1e-8
+    finally:
+        nmg.nmg_server_destroy(server)
+    # a hierarchy larger than the budget is refused at submission
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(min(sizes) // 2, 2, server))
+    try:
+        s, S = pool[0]
+        b = _rhs(s, 1)
+        x = torch.zeros_like(b)
+        t = C.c_uint64()
+        assert nmg.nmg_submit(server, S.handle, b, x, solve_opts(), t) == nmg.NMG_ERR_OOM
+    finally:
+        nmg.nmg_server_destroy(server)
