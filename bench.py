@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="nmg", choices=["nmg", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="V-cycle precision: 0 FP64, 1 FP32, 2 BF16")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent"],
+                    help="V-cycle engine (auto: the autotuner picks it on the first solve)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true",
                     help="serving workload: Poisson stream of solves over resident 2d/3d hierarchies")
@@ -189,6 +191,8 @@ def peaks():
 
 
 def gpu_arm(args):
+    import ctypes as C
+
     import numpy as np
     import torch
 
@@ -214,18 +218,20 @@ def gpu_arm(args):
     x = torch.empty_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     use_graph = 0 if args.no_graph else 1
+    engine = {"auto": nmg.NMG_ENGINE_AUTO, "kernels": nmg.NMG_ENGINE_KERNELS,
+              "persistent": nmg.NMG_ENGINE_PERSISTENT}[args.engine]
 
-    def timed_solves(prec, k, graph, profile=False):
+    def timed_solves(prec, k, graph, profile=0, engine=engine):
         times, infos = [], []
         if profile:
-            nmg.check(nmg.nmg_profile_enable(S.handle, 1))
+            nmg.check(nmg.nmg_profile_enable(S.handle, profile))
         with torch.cuda.stream(stream):
             for _ in range(k):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                info = S.solve(b, x, precision=prec, use_graph=graph)
+                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -256,8 +262,12 @@ def gpu_arm(args):
         dist.barrier()
     clk = clocks.stop()
 
-    # the V-cycle (the dominant launch) timed with events on its launch stream, same configuration
-    ptimes, pinfos, prof = timed_solves(args.precision, args.steps, use_graph, profile=True)
+    # the dominant kernel (finest-level Vanka apply) timed per launch with events on its launch
+    # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
+    ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
+    _, _, vprof = timed_solves(args.precision, args.steps, use_graph, profile=1)
+    rep = C.create_string_buffer(8192)
+    nmg.check(nmg.nmg_autotune_report(S.handle, rep, 8192))
     # plain FP64 path on the same mesh
     t64, i64, _ = timed_solves(nmg.NMG_PREC_FP64, args.steps, use_graph)
 
@@ -285,6 +295,7 @@ def gpu_arm(args):
 
     hbm, peak_kind = peaks()
     kms, klaunch, kbytes = prof
+    vms, vcount, vbytes = vprof
     achieved = kbytes / (kms / klaunch * 1e-3) / 1e9 if klaunch else None
     xr = x.cpu().numpy()
     line = {
@@ -313,13 +324,17 @@ def gpu_arm(args):
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
                       "speedup_of_mixed": statistics.mean(t64) / ms},
-        "roofline": {"kernel": ("V-cycle: one persistent cooperative kernel" if infos[-1].engine == 2 else
-                                "V-cycle: CUDA graph of per-step kernels"), "bound": "hbm",
+        "roofline": {"kernel": ("k_vanka_apply_staged2d" if sysm.problem.dim == 2 else "k_vanka_apply") +
+                               " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
-                     "timed": f"{klaunch} V-cycles over {args.steps} solves (events around each V-cycle)"},
+                     "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
+        "vcycle": {"ms": vms / vcount if vcount else None, "bytes": vbytes,
+                   "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
+                   "engine": {1: "per-step kernels (CUDA graph)", 2: "persistent kernel"}.get(infos[-1].engine)},
+        "autotune": json.loads(rep.value.decode()),
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.launches for i in infos)),

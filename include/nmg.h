@@ -209,17 +209,25 @@ nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* 
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int precision, int64_t first,
                                   int64_t count, double* out);
 
+/* The V-cycle autotuner's choices (engine and one-CTA tail threshold per
+ * precision) and its last trial timings, as a NUL-terminated JSON object in
+ * buf (len bytes).  NMG_ERR_INVALID if buf is too small. */
+nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len);
+
 /* Bytes of device memory held by the hierarchy. */
 nmg_status nmg_hierarchy_bytes(nmg_hierarchy* h, size_t* bytes);
 
 /* Releases every device allocation of the hierarchy; h is invalid afterwards. */
 nmg_status nmg_destroy_hierarchy(nmg_hierarchy* h);
 
-/* ---- kernel timing: when enabled, the finest-level Vanka apply launches of
- * later solves are bracketed by CUDA events on the hierarchy's stream. */
-nmg_status nmg_profile_enable(nmg_hierarchy* h, int enable);
-/* Total milliseconds and launch count of the timed launches since enabling,
- * and the algorithmic bytes one such launch moves. */
+/* ---- kernel timing on the hierarchy's stream.  mode 1: every V-cycle of
+ * later solves is bracketed by CUDA events; mode 2: every finest-level Vanka
+ * apply launch is (plain launches only: use_graph = 0, engine KERNELS);
+ * mode 0: off. */
+nmg_status nmg_profile_enable(nmg_hierarchy* h, int mode);
+/* Total milliseconds and count of the timed V-cycles / launches since enabling,
+ * and the algorithmic bytes one of them moves (every patch inverse, matrix and
+ * vector it must read or write once). */
 nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launches,
                             double* bytes_per_launch);
 

@@ -121,6 +121,13 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         cudaMemsetAsync(x, 0, g.nodes * g.nc * sizeof(T), s);
         return;
     }
+    const bool prof = h->prof == 2 && l == h->L - 1;
+    if (prof) {
+        const double sv = (double)sizeof(T);
+        const double si = prec == NMG_PREC_FP64 ? 8.0 : prec == NMG_PREC_FP32 ? 4.0 : 2.0;
+        h->prof_bytes = (double)g.patches * g.np * g.np * si + (double)g.nodes * g.nc * sv +
+                        (double)g.patches * g.np * sv;
+    }
     for (int st = 0; st < steps; ++st) {
         const T* d;
         if (st == 0 && x_zero) {
@@ -129,6 +136,8 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
             launch_spmv<T>(g, (const T*)P.A, x, b, (T*)P.r, true, s);
             d = (const T*)P.r;
         }
+        const bool rec = prof && h->prof_used < (int)h->prof_ev.size() / 2;
+        if (rec) cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
         if (prec == NMG_PREC_FP64)
             launch_vanka_apply<double, double>(g, (const double*)P.inv, P.inv_stride, (const double*)d, (double*)P.corr, s);
         else if (prec == NMG_PREC_FP32)
@@ -136,6 +145,10 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         else
             launch_vanka_apply<float, __nv_bfloat16>(g, (const __nv_bfloat16*)P.inv, P.inv_stride, (const float*)d,
                                                     (float*)P.corr, s);
+        if (rec) {
+            cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
+            h->prof_used++;
+        }
         launch_vanka_update<T>(g, (const T*)P.corr, x, st == 0 && x_zero, omega, average, s);
     }
 }
@@ -151,14 +164,19 @@ static void run_vcycle(Hierarchy* h, int prec, int nu1, int nu2, double omega, i
     const T om = (T)omega;
     auto bptr = [&](int l) -> T* { return (l == Lc - 1 && b_fine) ? const_cast<T*>(b_fine) : (T*)h->lev[l].p[prec].b; };
     auto xptr = [&](int l) -> T* { return (l == Lc - 1 && x_fine) ? x_fine : (T*)h->lev[l].p[prec].x; };
-    for (int l = Lc - 1; l >= 1; --l) {
+    // levels 0..c (all with at most tail_patches patches) run as one single-CTA kernel
+    int c = -1;
+    if (h->tail_patches[prec] > 0)
+        for (int l = 0; l < Lc && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
+    for (int l = Lc - 1; l >= 1 && l > c; --l) {
         Level& L = h->lev[l];
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu1, true, om, avg);
         launch_spmv<T>(L.g, (const T*)L.p[prec].A, xptr(l), bptr(l), (T*)L.p[prec].r, true, s);
         launch_restrict<T>(L.g, h->lev[l - 1].g, (const T*)L.p[prec].r, bptr(l - 1), h->lev[l - 1].mask, s);
     }
-    launch_coarse_gemv<T>(h->coarse_inv, h->n0, bptr(0), xptr(0), s);
-    for (int l = 1; l < Lc; ++l) {
+    if (c >= 0) launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, bptr(c), xptr(c));
+    else launch_coarse_gemv<T>(h->coarse_inv, h->n0, bptr(0), xptr(0), s);
+    for (int l = c >= 1 ? c + 1 : 1; l < Lc; ++l) {
         Level& L = h->lev[l];
         launch_prolong_add<T>(L.g, h->lev[l - 1].g, xptr(l - 1), xptr(l), L.mask, s);
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu2, false, om, avg);
@@ -174,7 +192,7 @@ static void vcycle_dispatch(Hierarchy* h, int prec, const nmg_solve_opts& o, con
 
 // Replays (capturing first if needed) the V-cycle on the level buffers as a CUDA graph.
 static nmg_status vcycle_graph(Hierarchy* h, int prec, const nmg_solve_opts& o) {
-    const int key[4] = {o.nu1, o.nu2, o.weighting, 1};
+    const int key[4] = {o.nu1, o.nu2, o.weighting, h->tail_patches[prec]};
     bool match = h->vgraph[prec] && std::memcmp(key, h->vgraph_key[prec], sizeof(key)) == 0 &&
                  h->vgraph_omega[prec] == o.omega;
     if (!match) {
@@ -182,8 +200,8 @@ static nmg_status vcycle_graph(Hierarchy* h, int prec, const nmg_solve_opts& o) 
         h->vgraph[prec] = nullptr;
         cudaGraph_t graph;
         NMG_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        const bool prof = h->prof;
-        h->prof = false;   // no event nodes inside the graph
+        const int prof = h->prof;
+        h->prof = 0;   // no event nodes inside the graph
         const int64_t before = g_launches;
         vcycle_dispatch(h, prec, o, nullptr, nullptr);
         h->vgraph_nodes[prec] = g_launches - before;
@@ -258,9 +276,11 @@ static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) 
     return NMG_OK;
 }
 
-// Engine for these options: AUTO times both engines on this hierarchy (the
-// finest right-hand side zeroed, so the traffic is the real one) and keeps
-// the faster; the choice is cached per precision and (nu1, nu2, weighting).
+// Autotuner.  For AUTO the V-cycle shape is picked by timing the candidates
+// on this hierarchy (finest right-hand side zeroed, so the memory traffic is
+// the real one): the per-step-kernel engine with the one-CTA tail covering
+// levels of at most {0, 16, 64, 256, 1024} patches, and the persistent engine.
+// The fastest is kept per precision and (nu1, nu2, weighting).
 static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* engine) {
     if (o.engine != NMG_ENGINE_AUTO) {
         *engine = o.engine;
@@ -278,23 +298,37 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     cudaEvent_t e0, e1;
     NMG_CK(cudaEventCreate(&e0));
     NMG_CK(cudaEventCreate(&e1));
+    struct Cand { int engine, tail; };
+    std::vector<Cand> cands;
+    int last_level = -2;
+    for (int tail : {0, 16, 64, 256, 1024}) {
+        int c = -1;
+        if (tail > 0)
+            for (int l = 0; l < h->L && (l == 0 || h->lev[l].g.patches <= tail); ++l) c = l;
+        if (c != last_level) cands.push_back({NMG_ENGINE_KERNELS, tail});
+        last_level = c;
+    }
+    cands.push_back({NMG_ENGINE_PERSISTENT, h->tail_patches[prec]});
     double best = 1e300;
-    int pick = NMG_ENGINE_KERNELS;
+    Cand pick = cands[0];
     const int64_t launches0 = g_launches;
-    for (int eng = NMG_ENGINE_KERNELS; eng <= NMG_ENGINE_PERSISTENT; ++eng) {
+    const int saved_tail = h->tail_patches[prec];
+    h->tuning.clear();
+    for (const Cand& cd : cands) {
+        h->tail_patches[prec] = cd.tail;
         bool ok = true;
-        for (int rep = 0; rep < 2 && ok; ++rep) ok = run_engine(h, o, eng) == NMG_OK;
+        for (int rep = 0; rep < 2 && ok; ++rep) ok = run_engine(h, o, cd.engine) == NMG_OK;
         cudaEventRecord(e0, h->stream);
-        for (int rep = 0; rep < 5 && ok; ++rep) ok = run_engine(h, o, eng) == NMG_OK;
+        for (int rep = 0; rep < 5 && ok; ++rep) ok = run_engine(h, o, cd.engine) == NMG_OK;
         cudaEventRecord(e1, h->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
         float ms = 0.f;
+        double us = -1.0;
         if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
-            h->engine_us[prec][eng - 1] = 1000.0 * ms / 5.0;
-            if (ms < best) { best = ms; pick = eng; }
-        } else {
-            h->engine_us[prec][eng - 1] = -1.0;
+            us = 1000.0 * ms / 5.0;
+            if (us < best) { best = us; pick = cd; }
         }
+        h->tuning.push_back({cd.engine, cd.tail, us});
         cudaGetLastError();
     }
     g_launches = launches0;
@@ -304,11 +338,12 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
     if (f[FLAG_ABORT]) {   // a persistent trial aborted: never pick it
         NMG_CK(cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int)));
-        pick = NMG_ENGINE_KERNELS;
+        if (pick.engine == NMG_ENGINE_PERSISTENT) pick = {NMG_ENGINE_KERNELS, saved_tail};
     }
-    h->engine_choice[prec] = pick;
+    h->tail_patches[prec] = pick.tail;
+    h->engine_choice[prec] = pick.engine;
     std::memcpy(h->engine_key[prec], key, sizeof(key));
-    *engine = pick;
+    *engine = pick.engine;
     return NMG_OK;
 }
 
@@ -319,14 +354,14 @@ static nmg_status vcycle_any(Hierarchy* h, const nmg_solve_opts& o, const void* 
     const int prec = o.precision;
     int engine = 0;
     NMG_TRY(resolve_engine(h, o, &engine));
-    if (prec == NMG_PREC_FP64 && engine == NMG_ENGINE_KERNELS && !o.use_graph && !h->prof) {
+    if (prec == NMG_PREC_FP64 && engine == NMG_ENGINE_KERNELS && !o.use_graph && h->prof != 1) {
         run_vcycle<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, (const double*)v, (double*)z);
         return NMG_OK;
     }
     const size_t vs = prec == NMG_PREC_FP64 ? sizeof(double) : sizeof(float);
     if (prec != NMG_PREC_FP64 && fp64_io) launch_convert<double, float>((const double*)v, (float*)F.p[prec].b, n, h->stream);
     else NMG_CK(cudaMemcpyAsync(F.p[prec].b, v, n * vs, cudaMemcpyDeviceToDevice, h->stream));
-    const bool rec = h->prof && h->prof_used < (int)h->prof_ev.size() / 2;
+    const bool rec = h->prof == 1 && h->prof_used < (int)h->prof_ev.size() / 2;
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
         h->prof_bytes = vcycle_bytes(h, prec, o.nu1, o.nu2);
@@ -952,11 +987,34 @@ nmg_status nmg_profile_enable(nmg_hierarchy* h, int enable) {
         for (auto& e : h->prof_ev)
             if (cudaEventCreate(&e) != cudaSuccess) return fail(NMG_ERR_CUDA, "event creation failed");
     }
-    h->prof = enable != 0;
+    if (enable < 0 || enable > 2) return fail(NMG_ERR_INVALID, "profile mode must be 0, 1 or 2");
+    h->prof = enable;
     h->prof_used = 0;
     h->prof_ms = 0.0;
     h->prof_launches = 0;
     h->prof_bytes = 0.0;
+    return NMG_OK;
+}
+
+nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
+    if (!h || !buf || len == 0) return fail(NMG_ERR_INVALID, "NULL argument");
+    std::string js = "{\"choice\": [";
+    for (int p = 0; p < 3; ++p) {
+        js += "{\"precision\": " + std::to_string(p) + ", \"engine\": " + std::to_string(h->engine_choice[p]) +
+              ", \"tail_patches\": " + std::to_string(h->tail_patches[p]) + "}";
+        if (p < 2) js += ", ";
+    }
+    js += "], \"last_trials\": [";
+    for (size_t i = 0; i < h->tuning.size(); ++i) {
+        char tmp[160];
+        std::snprintf(tmp, sizeof(tmp), "{\"engine\": %d, \"tail_patches\": %d, \"us_per_vcycle\": %.3f}",
+                      h->tuning[i].engine, h->tuning[i].tail, h->tuning[i].us);
+        js += tmp;
+        if (i + 1 < h->tuning.size()) js += ", ";
+    }
+    js += "]}";
+    if (js.size() + 1 > len) return fail(NMG_ERR_INVALID, "buffer too small");
+    std::memcpy(buf, js.c_str(), js.size() + 1);
     return NMG_OK;
 }
 

@@ -92,15 +92,27 @@ __device__ __forceinline__ void apply_patch(const TS* Ap, const T* sd, T* __rest
     T acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = T(0);
-#pragma unroll 4
-    for (int j = 0; j < NP; ++j) {
-        const T dj = sd[j];
+    if (DIM == 2) {
+        // 27 columns: issue all loads first so they are in flight together (one
+        // memory latency per patch instead of one per column), then sum in order
+        if (lane < NP) {
+            TS a[NP];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int row = lane + 32 * q;
-            if (row < NP) {
-                const TS a = GLOBAL ? ldg(Ap + j * NP + row) : Ap[j * NP + row];
-                acc[q] = fma(Cvt<T, TS>::f(a), dj, acc[q]);
+            for (int j = 0; j < NP; ++j) a[j] = GLOBAL ? ldg(Ap + j * NP + lane) : Ap[j * NP + lane];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc[0] = fma(Cvt<T, TS>::f(a[j]), sd[j], acc[0]);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < NP; ++j) {
+            const T dj = sd[j];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int row = lane + 32 * q;
+                if (row < NP) {
+                    const TS a = GLOBAL ? ldg(Ap + j * NP + row) : Ap[j * NP + row];
+                    acc[q] = fma(Cvt<T, TS>::f(a), dj, acc[q]);
+                }
             }
         }
     }

@@ -86,7 +86,7 @@ struct Hierarchy {
     int vgraph_key[3][4] = {};    // nu1, nu2, weighting, omega bits hash
     double vgraph_omega[3] = {0, 0, 0};
     // profiling of the finest-level Vanka apply
-    bool prof = false;
+    int prof = 0;                        // 0 off, 1 events per V-cycle, 2 per finest-level Vanka apply
     std::vector<cudaEvent_t> prof_ev;   // pairs
     int prof_used = 0;
     double prof_ms = 0.0;
@@ -96,8 +96,12 @@ struct Hierarchy {
     // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
     unsigned* pbar = nullptr;
     int engine_choice[3] = {0, 0, 0};
+    int tail_patches[3] = {0, 0, 0};     // levels with at most this many patches run in the one-CTA tail
+                                         // (0: none; the autotuner may pick a threshold)
     int engine_key[3][3] = {};
     double engine_us[3][2] = {};
+    struct Trial { int engine, tail; double us; };
+    std::vector<Trial> tuning;             // the autotuner's last measurements
     double prof_bytes = 0.0;
     std::vector<void*> allocs;
 };
@@ -109,6 +113,9 @@ enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_AB
 struct Hierarchy;
 cudaError_t launch_vcycle_persistent(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting,
                                      unsigned* bar, int* abort, int small_patches);
+// Levels 0..top of a V-cycle on one CTA (persistent.cu).
+void launch_vcycle_tail(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
+                        const void* b_top, void* x_top);
 
 // ---------------------------------------------------------------------------
 // Launchers (setup_kernels.cu)

@@ -108,6 +108,7 @@ _SIGS = {
     "nmg_destroy_hierarchy": [_H],
     "nmg_profile_enable": [_H, C.c_int],
     "nmg_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "nmg_autotune_report": [_H, C.c_char_p, C.c_size_t],
     "nmg_server_create": [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)],
     "nmg_submit": [C.c_void_p, _H, _P, _P, C.POINTER(nmg_solve_opts), C.POINTER(C.c_uint64)],
     "nmg_poll": [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(nmg_solve_info)],
@@ -233,3 +234,7 @@ def nmg_poll(server, ticket, timeout_ms, info: nmg_solve_info) -> int:
 
 def nmg_server_destroy(server) -> int:
     return _lib.nmg_server_destroy(server)
+
+
+def nmg_autotune_report(h, buf, length) -> int:
+    return _lib.nmg_autotune_report(h, buf, length)
