@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="nmg", choices=["nmg", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="V-cycle precision: 0 FP64, 1 FP32, 2 BF16")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent"],
+    ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent", "fused"],
                     help="V-cycle engine (auto: the autotuner picks it on the first solve)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true",
@@ -219,7 +219,7 @@ def gpu_arm(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     use_graph = 0 if args.no_graph else 1
     engine = {"auto": nmg.NMG_ENGINE_AUTO, "kernels": nmg.NMG_ENGINE_KERNELS,
-              "persistent": nmg.NMG_ENGINE_PERSISTENT}[args.engine]
+              "persistent": nmg.NMG_ENGINE_PERSISTENT, "fused": nmg.NMG_ENGINE_FUSED}[args.engine]
 
     def timed_solves(prec, k, graph, profile=0, engine=engine):
         times, infos = [], []
@@ -317,7 +317,7 @@ def gpu_arm(args):
                    "l2": "flushed before every solve (256 MB write, outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": infos[-1].iterations,
-        "engine": {1: "kernels", 2: "persistent"}.get(infos[-1].engine, "?"),
+        "engine": {1: "kernels", 2: "persistent", 3: "fused"}.get(infos[-1].engine, "?"),
         "rel_residual": infos[-1].rel_residual,
         "solves_per_s": world * 1000.0 / ms_max,
         "p50_ms": statistics.median(times),
@@ -333,7 +333,8 @@ def gpu_arm(args):
                      "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
         "vcycle": {"ms": vms / vcount if vcount else None, "bytes": vbytes,
                    "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
-                   "engine": {1: "per-step kernels (CUDA graph)", 2: "persistent kernel"}.get(infos[-1].engine)},
+                   "engine": {1: "per-step kernels", 2: "persistent kernel",
+                              3: "per-step kernels, fused update/prolongation + residual"}.get(infos[-1].engine)},
         "autotune": json.loads(rep.value.decode()),
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},

@@ -94,9 +94,12 @@ typedef struct {
 } nmg_solve_opts;
 
 /* V-cycle execution engines (same arithmetic, same results). */
-#define NMG_ENGINE_AUTO       0  /* time both engines on this hierarchy at first use, keep the faster */
+#define NMG_ENGINE_AUTO       0  /* time the engines (and the tail threshold) on this hierarchy at first
+                                    use and keep the fastest (nmg_autotune_report shows the trials)   */
 #define NMG_ENGINE_KERNELS    1  /* one kernel per step (optionally replayed as a CUDA graph)         */
 #define NMG_ENGINE_PERSISTENT 2  /* one cooperative persistent kernel per V-cycle                     */
+#define NMG_ENGINE_FUSED      3  /* per-step kernels, each Vanka update and each prolongation fused
+                                    into the residual that follows it (fewer, heavier kernels)        */
 
 typedef struct {
     int iterations;       /* total FGMRES iterations                                      */

@@ -183,7 +183,100 @@ static void run_vcycle(Hierarchy* h, int prec, int nu1, int nu2, double omega, i
     }
 }
 
+// The same V-cycle on the level buffers with fewer kernels: each Vanka update
+// is fused into the residual that follows it, the prolongation into the first
+// post-smoothing residual (the iterate alternates between the buffers x and
+// x2 of a level; every level's final iterate ends in x).  The element code and
+// its order are those of run_vcycle, so the results are bitwise identical.
+template <typename T>
+static void run_vcycle_fused(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting) {
+    const int Lc = h->L;
+    cudaStream_t s = h->stream;
+    const bool avg = weighting == NMG_WEIGHT_AVERAGE;
+    const T om = (T)omega;
+    int c = -1;
+    if (h->tail_patches[prec] > 0)
+        for (int l = 0; l < Lc && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
+    T* cur_level[kMaxLevels] = {};
+    auto apply = [&](int l, const T* d) {
+        PrecData& P = h->lev[l].p[prec];
+        const Geom& g = h->lev[l].g;
+        if (prec == NMG_PREC_FP64)
+            launch_vanka_apply<double, double>(g, (const double*)P.inv, P.inv_stride, (const double*)d, (double*)P.corr, s);
+        else if (prec == NMG_PREC_FP32)
+            launch_vanka_apply<float, float>(g, (const float*)P.inv, P.inv_stride, (const float*)d, (float*)P.corr, s);
+        else
+            launch_vanka_apply<float, __nv_bfloat16>(g, (const __nv_bfloat16*)P.inv, P.inv_stride, (const float*)d,
+                                                    (float*)P.corr, s);
+    };
+    for (int l = Lc - 1; l >= 1 && l > c; --l) {
+        Level& L = h->lev[l];
+        PrecData& P = L.p[prec];
+        T* X = (T*)P.x;
+        T* Y = (T*)P.x2;
+        const T* A = (const T*)P.A;
+        const T* b = (const T*)P.b;
+        T* r = (T*)P.r;
+        const T* corr = (const T*)P.corr;
+        T* bufs[2] = {X, Y};
+        int nb = 0;
+        const T* cur = X;
+        if (nu1 == 0) {
+            cudaMemsetAsync(X, 0, L.g.nodes * L.g.nc * sizeof(T), s);
+            launch_restrict<T>(L.g, h->lev[l - 1].g, b, (T*)h->lev[l - 1].p[prec].b, h->lev[l - 1].mask, s);
+        } else {
+            bool zero = true;
+            apply(l, b);
+            for (int st = 1; st <= nu1; ++st) {   // the last pass gives the residual for the restriction
+                T* out = bufs[nb];
+                nb ^= 1;
+                launch_update_residual<T>(L.g, A, corr, zero ? nullptr : cur, zero, om, avg, b, out, r, s);
+                cur = out;
+                zero = false;
+                if (st < nu1) apply(l, r);
+            }
+            launch_restrict<T>(L.g, h->lev[l - 1].g, r, (T*)h->lev[l - 1].p[prec].b, h->lev[l - 1].mask, s);
+        }
+        cur_level[l] = const_cast<T*>(cur);
+    }
+    if (c >= 0) launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, nullptr, nullptr);
+    else launch_coarse_gemv<T>(h->coarse_inv, h->n0, (const T*)h->lev[0].p[prec].b, (T*)h->lev[0].p[prec].x, s);
+    for (int l = c >= 1 ? c + 1 : 1; l < Lc; ++l) {
+        Level& L = h->lev[l];
+        PrecData& P = L.p[prec];
+        T* X = (T*)P.x;
+        T* Y = (T*)P.x2;
+        const T* A = (const T*)P.A;
+        const T* b = (const T*)P.b;
+        T* r = (T*)P.r;
+        const T* corr = (const T*)P.corr;
+        const T* ec = (const T*)h->lev[l - 1].p[prec].x;
+        T* cur = cur_level[l];
+        if (nu2 == 0) {
+            launch_prolong_add<T>(L.g, h->lev[l - 1].g, ec, cur, L.mask, s);
+            if (cur != X) cudaMemcpyAsync(X, cur, L.g.nodes * L.g.nc * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            continue;
+        }
+        T* out = cur == X ? Y : X;
+        launch_prolong_residual<T>(L.g, h->lev[l - 1].g, A, ec, cur, L.mask, b, out, r, s);
+        cur = out;
+        apply(l, r);
+        for (int st = 1; st < nu2; ++st) {
+            out = cur == X ? Y : X;
+            launch_update_residual<T>(L.g, A, corr, cur, false, om, avg, b, out, r, s);
+            cur = out;
+            apply(l, r);
+        }
+        launch_vanka_update2<T>(L.g, corr, cur, X, false, om, avg, s);
+    }
+}
+
 static void vcycle_dispatch(Hierarchy* h, int prec, const nmg_solve_opts& o, const void* b, void* x) {
+    if (h->fused[prec] && !b && !x) {
+        if (prec == NMG_PREC_FP64) run_vcycle_fused<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting);
+        else run_vcycle_fused<float>(h, prec, o.nu1, o.nu2, o.omega, o.weighting);
+        return;
+    }
     if (prec == NMG_PREC_FP64)
         run_vcycle<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, (const double*)b, (double*)x);
     else
@@ -192,7 +285,7 @@ static void vcycle_dispatch(Hierarchy* h, int prec, const nmg_solve_opts& o, con
 
 // Replays (capturing first if needed) the V-cycle on the level buffers as a CUDA graph.
 static nmg_status vcycle_graph(Hierarchy* h, int prec, const nmg_solve_opts& o) {
-    const int key[4] = {o.nu1, o.nu2, o.weighting, h->tail_patches[prec]};
+    const int key[4] = {o.nu1, o.nu2, o.weighting, 2 * h->tail_patches[prec] + h->fused[prec]};
     bool match = h->vgraph[prec] && std::memcmp(key, h->vgraph_key[prec], sizeof(key)) == 0 &&
                  h->vgraph_omega[prec] == o.omega;
     if (!match) {
@@ -232,7 +325,7 @@ static nmg_status validate_opts(const nmg_solve_opts* o) {
     if (!(o->rtol >= 0.0) || o->restart < 1 || o->restart > kMaxRestart || o->maxit < 0 || o->nu1 < 0 ||
         o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64 || !std::isfinite(o->omega) ||
         (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM) ||
-        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_PERSISTENT)
+        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_FUSED)
         return fail(NMG_ERR_INVALID, "invalid solve options");
     return NMG_OK;
 }
@@ -271,6 +364,7 @@ static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) 
                                         64));
         return NMG_OK;
     }
+    h->fused[prec] = engine == NMG_ENGINE_FUSED;
     if (o.use_graph) return vcycle_graph(h, prec, o);
     vcycle_dispatch(h, prec, o, nullptr, nullptr);
     return NMG_OK;
@@ -298,24 +392,25 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     cudaEvent_t e0, e1;
     NMG_CK(cudaEventCreate(&e0));
     NMG_CK(cudaEventCreate(&e1));
-    struct Cand { int engine, tail; };
+    struct Cand { int engine, tail, fused; };
     std::vector<Cand> cands;
     int last_level = -2;
-    for (int tail : {0, 16, 64, 256, 1024}) {
+    for (int tail : {0, 16, 64}) {
         int c = -1;
         if (tail > 0)
             for (int l = 0; l < h->L && (l == 0 || h->lev[l].g.patches <= tail); ++l) c = l;
-        if (c != last_level) cands.push_back({NMG_ENGINE_KERNELS, tail});
+        if (c != last_level)
+            for (int fz : {0, 1}) cands.push_back({fz ? NMG_ENGINE_FUSED : NMG_ENGINE_KERNELS, tail, fz});
         last_level = c;
     }
-    cands.push_back({NMG_ENGINE_PERSISTENT, h->tail_patches[prec]});
+    cands.push_back({NMG_ENGINE_PERSISTENT, 0, 0});
     double best = 1e300;
     Cand pick = cands[0];
     const int64_t launches0 = g_launches;
-    const int saved_tail = h->tail_patches[prec];
     h->tuning.clear();
     for (const Cand& cd : cands) {
         h->tail_patches[prec] = cd.tail;
+        h->fused[prec] = cd.fused;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) ok = run_engine(h, o, cd.engine) == NMG_OK;
         cudaEventRecord(e0, h->stream);
@@ -328,7 +423,7 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
             us = 1000.0 * ms / 5.0;
             if (us < best) { best = us; pick = cd; }
         }
-        h->tuning.push_back({cd.engine, cd.tail, us});
+        h->tuning.push_back({cd.engine, cd.tail, cd.fused, us});
         cudaGetLastError();
     }
     g_launches = launches0;
@@ -338,13 +433,45 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
     if (f[FLAG_ABORT]) {   // a persistent trial aborted: never pick it
         NMG_CK(cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int)));
-        if (pick.engine == NMG_ENGINE_PERSISTENT) pick = {NMG_ENGINE_KERNELS, saved_tail};
+        if (pick.engine == NMG_ENGINE_PERSISTENT) pick = cands[0];
     }
+    h->fused[prec] = pick.fused;
     h->tail_patches[prec] = pick.tail;
     h->engine_choice[prec] = pick.engine;
     std::memcpy(h->engine_key[prec], key, sizeof(key));
     *engine = pick.engine;
     return NMG_OK;
+}
+
+// One V-cycle on the finest level's own buffers (b -> x) with the engine the
+// options (or the autotuner) select; bracketed by events in profiling mode 1.
+static nmg_status vcycle_in_place(Hierarchy* h, const nmg_solve_opts& o) {
+    int engine = 0;
+    NMG_TRY(resolve_engine(h, o, &engine));
+    const bool rec = h->prof == 1 && h->prof_used < (int)h->prof_ev.size() / 2;
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_used], h->stream);
+        h->prof_bytes = vcycle_bytes(h, o.precision, o.nu1, o.nu2);
+    }
+    NMG_TRY(run_engine(h, o, engine));
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], h->stream);
+        h->prof_used++;
+    }
+    return NMG_OK;
+}
+
+// v = w * scal[S_INVH] (the next FP64 Krylov vector), also written as the
+// right-hand side of the next V-cycle (converted for reduced precision).
+static cudaError_t scale_into_vcycle_input(Hierarchy* h, const nmg_solve_opts& o, const double* w, double* v) {
+    Level& F = h->lev[h->L - 1];
+    const int64_t n = F.g.nodes * F.g.nc;
+    if (o.precision == NMG_PREC_FP64) {
+        launch_scale_convert(w, h->scal + S_INVH, v, nullptr, n, h->stream);
+        return cudaMemcpyAsync(F.p[NMG_PREC_FP64].b, v, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    }
+    launch_scale_convert(w, h->scal + S_INVH, v, (float*)F.p[o.precision].b, n, h->stream);
+    return cudaGetLastError();
 }
 
 // z = V-cycle(v) for vectors of the precision's arithmetic type or FP64 (converted).
@@ -355,6 +482,7 @@ static nmg_status vcycle_any(Hierarchy* h, const nmg_solve_opts& o, const void* 
     int engine = 0;
     NMG_TRY(resolve_engine(h, o, &engine));
     if (prec == NMG_PREC_FP64 && engine == NMG_ENGINE_KERNELS && !o.use_graph && h->prof != 1) {
+        h->fused[prec] = 0;
         run_vcycle<double>(h, prec, o.nu1, o.nu2, o.omega, o.weighting, (const double*)v, (double*)z);
         return NMG_OK;
     }
@@ -454,7 +582,7 @@ static void job_enqueue_cycle(SolveJob& J) {
     launch_spmv<double>(g, h->lev[h->L - 1].A64, h->x64, h->b64, h->w64, true, s);
     launch_norm2(h->w64, n, h->partial, h->scal + S_BETA, s);
     launch_start_cycle(h->scal, J.o.restart, s);
-    launch_scale(h->w64, h->scal + S_INVH, false, h->V, n, s);
+    JOB_CK(scale_into_vcycle_input(h, J.o, h->w64, h->V));
     JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     J.phase = SolveJob::P_CYCLE;
 }
@@ -465,22 +593,27 @@ static void job_enqueue_iter(SolveJob& J) {
     const int64_t n = g.nodes * g.nc;
     const int j = J.j, m = J.o.restart;
     cudaStream_t s = h->stream;
-    double* vj = h->V + (int64_t)j * n;
     double* zj = h->Z + (int64_t)j * n;
-    const nmg_status st = precondition(h, J.o, vj, zj);
+    // z_j = M^{-1} v_j: v_j is already the V-cycle's right-hand side (written by
+    // the scaling that produced it), the result stays in the level buffer
+    const nmg_status st = vcycle_in_place(h, J.o);
     if (st != NMG_OK) {
         job_fail(J, st);
         J.phase = SolveJob::P_DONE;
         return;
     }
-    launch_spmv<double>(g, h->lev[h->L - 1].A64, zj, nullptr, h->w64, false, s);
-    // classical Gram-Schmidt, two passes
-    launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_HC, false, s);
+    const PrecData& PF = h->lev[h->L - 1].p[J.o.precision];
+    double* A64 = h->lev[h->L - 1].A64;
+    // w = A z_j (FP64), z_j stored as basis vector Z_j
+    if (J.o.precision == NMG_PREC_FP64) launch_spmv_zstore<double>(g, A64, (const double*)PF.x, zj, h->w64, s);
+    else launch_spmv_zstore<float>(g, A64, (const float*)PF.x, zj, h->w64, s);
+    // classical Gram-Schmidt, two passes; the second ends with ||w|| and the Givens update
+    launch_multidot_fused(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_HC, h->counters, s);
     launch_gs_update(h->V, n, j + 1, h->scal + S_HC, h->w64, n, h->partial, nullptr, false, s);
-    launch_multidot(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_Y, false, s);
-    launch_gs_update(h->V, n, j + 1, h->scal + S_Y, h->w64, n, h->partial, h->scal + S_HC + j + 1, true, s);
-    launch_arnoldi_finish(h->scal, j, m, s);
-    launch_scale(h->w64, h->scal + S_INVH, false, h->V + (int64_t)(j + 1) * n, n, s);
+    launch_multidot_fused(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_Y, h->counters, s);
+    launch_gs_norm_arnoldi(h->V, n, j + 1, h->scal + S_Y, h->w64, n, h->partial, h->scal, j, m, h->counters, s);
+    // v_{j+1} = w / h_{j+1,j}, also written as the next V-cycle's right-hand side
+    JOB_CK(scale_into_vcycle_input(h, J.o, h->w64, h->V + (int64_t)(j + 1) * n));
     JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     J.phase = SolveJob::P_ITER;
 }
@@ -729,8 +862,9 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
             return cleanup(fail(NMG_ERR_CUDA, "mask upload failed"));
         float* A32 = nullptr;
         if (low && (st = dalloc(h, (void**)&A32, mat * sizeof(float))) != NMG_OK) return cleanup(st);
-        void* fvec[4] = {nullptr, nullptr, nullptr, nullptr};   // float work vectors shared by FP32 / BF16
+        void* fvec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // float work vectors shared by FP32 / BF16
         if (low) {
+            if ((st = dalloc(h, &fvec[4], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
             for (int q = 0; q < 3; ++q)
                 if ((st = dalloc(h, &fvec[q], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
             if (l > 0 && (st = dalloc(h, &fvec[3], (size_t)g.patches * g.np * sizeof(float))) != NMG_OK) return cleanup(st);
@@ -740,12 +874,12 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
             PrecData& P = Lv.p[p];
             if (p == NMG_PREC_FP64) {
                 P.A = Lv.A64;
-                for (void** q : {&P.b, &P.x, &P.r})
+                for (void** q : {&P.b, &P.x, &P.r, &P.x2})
                     if ((st = dalloc(h, q, nvec * sizeof(double))) != NMG_OK) return cleanup(st);
                 if (l > 0 && (st = dalloc(h, &P.corr, (size_t)g.patches * g.np * sizeof(double))) != NMG_OK) return cleanup(st);
             } else {
                 P.A = A32;
-                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3];
+                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3]; P.x2 = fvec[4];
             }
             if (l > 0) {
                 P.inv_stride = pad16((int64_t)g.np * g.np, store_size(p));
@@ -762,6 +896,8 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if ((st = dalloc(h, (void**)&h->scal, S_COUNT * sizeof(double))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->flags, FLAG_COUNT * sizeof(int))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->pbar, 2 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
+    if ((st = dalloc(h, (void**)&h->counters, 4 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
+    if (cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
     if (cudaMemset(h->flags, 0, FLAG_COUNT * sizeof(int)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
     if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess)
@@ -1001,14 +1137,16 @@ nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
     std::string js = "{\"choice\": [";
     for (int p = 0; p < 3; ++p) {
         js += "{\"precision\": " + std::to_string(p) + ", \"engine\": " + std::to_string(h->engine_choice[p]) +
-              ", \"tail_patches\": " + std::to_string(h->tail_patches[p]) + "}";
+              ", \"tail_patches\": " + std::to_string(h->tail_patches[p]) +
+              ", \"fused\": " + std::to_string(h->fused[p]) + "}";
         if (p < 2) js += ", ";
     }
     js += "], \"last_trials\": [";
     for (size_t i = 0; i < h->tuning.size(); ++i) {
         char tmp[160];
-        std::snprintf(tmp, sizeof(tmp), "{\"engine\": %d, \"tail_patches\": %d, \"us_per_vcycle\": %.3f}",
-                      h->tuning[i].engine, h->tuning[i].tail, h->tuning[i].us);
+        std::snprintf(tmp, sizeof(tmp),
+                      "{\"engine\": %d, \"tail_patches\": %d, \"fused\": %d, \"us_per_vcycle\": %.3f}",
+                      h->tuning[i].engine, h->tuning[i].tail, h->tuning[i].fused, h->tuning[i].us);
         js += tmp;
         if (i + 1 < h->tuning.size()) js += ", ";
     }

@@ -36,10 +36,11 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
     return (int64_t)(2 * px + ax) + (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
 }
 
-// y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout).
-template <typename T, int DIM>
-__device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
-                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
+// y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
+// at a node j come from xval(j, xv) (loaded, converted or recomputed).
+template <typename T, int DIM, class XF>
+__device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
+                                            const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
@@ -57,8 +58,7 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
         if (ok) {
             const int64_t j = i + dx + dy * sy + dz * sz;
             T xv[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) xv[c] = x[j * NC + c];
+            xval(j, xv);
             const T* As = A + (int64_t)s * NB * g.ld + i;
 #pragma unroll
             for (int r = 0; r < NC; ++r)
@@ -68,6 +68,19 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
     }
 #pragma unroll
     for (int r = 0; r < NC; ++r) y[i * NC + r] = residual ? b[i * NC + r] - acc[r] : acc[r];
+}
+
+// y_i = (A x)_i or b_i - (A x)_i with x stored as TX (converted to T on load).
+template <typename T, int DIM, typename TX = T>
+__device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const TX* __restrict__ x,
+                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
+    spmv_node_f<T, DIM>(
+        g, A,
+        [&](int64_t j, T* xv) {
+#pragma unroll
+            for (int c = 0; c < DIM + 1; ++c) xv[c] = (T)x[j * (DIM + 1) + c];
+        },
+        b, y, residual, i);
 }
 
 // Gathers R_p d into sd[0..NP) (called by one warp; lane-strided).
@@ -123,11 +136,13 @@ __device__ __forceinline__ void apply_patch(const TS* Ap, const T* sd, T* __rest
     }
 }
 
-// x_i += w_i * (sum of the corrections of the patches containing node i), in
-// ascending patch order; w_i = omega / multiplicity ("average") or omega.
+// v = x_i + w_i * (sum of the corrections of the patches containing node i),
+// in ascending patch order; w_i = omega / multiplicity ("average") or omega;
+// x_i = 0 when x_zero (x is not read).
 template <typename T, int DIM>
-__device__ __forceinline__ void vanka_update_node(const Geom& g, const T* __restrict__ corr, T* __restrict__ x,
-                                                  bool x_zero, T omega, bool average, int64_t i) {
+__device__ __forceinline__ void vanka_update_value(const Geom& g, const T* __restrict__ corr,
+                                                   const T* __restrict__ x, bool x_zero, T omega, bool average,
+                                                   int64_t i, T* v) {
     constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     int xyz[3];
@@ -162,8 +177,32 @@ __device__ __forceinline__ void vanka_update_node(const Geom& g, const T* __rest
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const T old = x_zero ? T(0) : x[i * NC + c];
-        x[i * NC + c] = old + wgt * sum[c];
+        v[c] = fma(wgt, sum[c], old);
     }
+}
+
+// x_out_i = x_in_i + w_i * sum of the corrections (x_in may equal x_out).
+template <typename T, int DIM>
+__device__ __forceinline__ void vanka_update_node(const Geom& g, const T* __restrict__ corr, const T* x_in,
+                                                  T* x_out, bool x_zero, T omega, bool average, int64_t i) {
+    T v[DIM + 1];
+    vanka_update_value<T, DIM>(g, corr, x_in, x_zero, omega, average, i, v);
+#pragma unroll
+    for (int c = 0; c < DIM + 1; ++c) x_out[i * (DIM + 1) + c] = v[c];
+}
+
+// Fused: x_out_i = update of x_in at node i (as above) and
+// r_i = b_i - (A x_out)_i with x_out at the neighbours recomputed the same way.
+// x_out must not alias x_in.
+template <typename T, int DIM>
+__device__ __forceinline__ void update_residual_node(const Geom& g, const T* __restrict__ A,
+                                                     const T* __restrict__ corr, const T* __restrict__ x_in,
+                                                     bool x_zero, T omega, bool average, const T* __restrict__ b,
+                                                     T* __restrict__ x_out, T* __restrict__ r, int64_t i) {
+    vanka_update_node<T, DIM>(g, corr, x_in, x_out, x_zero, omega, average, i);
+    spmv_node_f<T, DIM>(
+        g, A, [&](int64_t j, T* xv) { vanka_update_value<T, DIM>(g, corr, x_in, x_zero, omega, average, j, xv); },
+        b, r, true, i);
 }
 
 // (r_c)_I = (P^T r_f)_I, zero on coarse Dirichlet entries.
@@ -197,10 +236,11 @@ __device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, cons
     for (int k = 0; k < NC; ++k) rc[I * NC + k] = cmask[I * NC + k] ? T(0) : sum[k];
 }
 
-// (x_f)_i += (P e_c)_i, fine Dirichlet entries untouched.
+// v = x_in_i + (P e_c)_i, x_in_i on fine Dirichlet entries.
 template <typename T, int DIM>
-__device__ __forceinline__ void prolong_node(const Geom& f, const Geom& c, const T* __restrict__ ec,
-                                             T* __restrict__ xf, const uint8_t* __restrict__ fmask, int64_t i) {
+__device__ __forceinline__ void prolong_value(const Geom& f, const Geom& c, const T* __restrict__ ec,
+                                              const T* __restrict__ x_in, const uint8_t* __restrict__ fmask,
+                                              int64_t i, T* v) {
     constexpr int NC = DIM + 1;
     int xyz[3];
     node_xyz(f, i, xyz[0], xyz[1], xyz[2]);
@@ -224,8 +264,32 @@ __device__ __forceinline__ void prolong_node(const Geom& f, const Geom& c, const
                 for (int k = 0; k < NC; ++k) sum[k] = fma(w, ec[I * NC + k], sum[k]);
             }
 #pragma unroll
-    for (int k = 0; k < NC; ++k)
-        if (!fmask[i * NC + k]) xf[i * NC + k] += sum[k];
+    for (int k = 0; k < NC; ++k) v[k] = fmask[i * NC + k] ? x_in[i * NC + k] : x_in[i * NC + k] + sum[k];
+}
+
+// (x_f)_i += (P e_c)_i, fine Dirichlet entries untouched.
+template <typename T, int DIM>
+__device__ __forceinline__ void prolong_node(const Geom& f, const Geom& c, const T* __restrict__ ec,
+                                             T* __restrict__ xf, const uint8_t* __restrict__ fmask, int64_t i) {
+    T v[DIM + 1];
+    prolong_value<T, DIM>(f, c, ec, xf, fmask, i, v);
+#pragma unroll
+    for (int k = 0; k < DIM + 1; ++k) xf[i * (DIM + 1) + k] = v[k];
+}
+
+// Fused: x_out_i = x_in_i + (P e_c)_i and r_i = b_i - (A x_out)_i with x_out at
+// the neighbours recomputed the same way.  x_out must not alias x_in.
+template <typename T, int DIM>
+__device__ __forceinline__ void prolong_residual_node(const Geom& f, const Geom& c, const T* __restrict__ A,
+                                                      const T* __restrict__ ec, const T* __restrict__ x_in,
+                                                      const uint8_t* __restrict__ fmask, const T* __restrict__ b,
+                                                      T* __restrict__ x_out, T* __restrict__ r, int64_t i) {
+    T v[DIM + 1];
+    prolong_value<T, DIM>(f, c, ec, x_in, fmask, i, v);
+#pragma unroll
+    for (int k = 0; k < DIM + 1; ++k) x_out[i * (DIM + 1) + k] = v[k];
+    spmv_node_f<T, DIM>(
+        f, A, [&](int64_t j, T* xv) { prolong_value<T, DIM>(f, c, ec, x_in, fmask, j, xv); }, b, r, true, i);
 }
 
 // x_row = (inv b)_row with FP64 sums, by one warp.

@@ -101,9 +101,7 @@ k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ pa
 // Column j of the Hessenberg matrix from scal[S_HC + 0..j+1] (h_{0..j,j} and
 // ||w||): apply the earlier rotations, build rotation j, update g, write the
 // residual estimate |g_{j+1}| / ||b|| and 1 / h_{j+1,j}.
-__global__ void k_arnoldi_finish(double* scal, int j, int m) {
-    NMG_PDL_ENTRY();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void arnoldi_column(double* scal, int j, int m) {
     double* H = scal + S_H + (int64_t)j * (m + 1);
     const double* hc = scal + S_HC;
     double* cs = scal + S_CS;
@@ -133,6 +131,12 @@ __global__ void k_arnoldi_finish(double* scal, int j, int m) {
     scal[S_INVH] = hnext != 0.0 ? 1.0 / hnext : 0.0;
     if (!isfinite(est) || !isfinite(hnext)) scal[S_STATUS] = (double)NMG_ERR_NONFINITE;
     scal[S_ITER] += 1.0;
+}
+
+__global__ void k_arnoldi_finish(double* scal, int j, int m) {
+    NMG_PDL_ENTRY();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    arnoldi_column(scal, j, m);
 }
 
 __global__ void k_start_cycle(double* scal, int m) {
@@ -192,6 +196,106 @@ inline unsigned grid_for(int64_t n) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+
+// Sum over the kDotBlocks partials of row k in the fixed order of
+// k_finish_dots (lane-strided, then a shuffle tree); valid in lane 0.
+__device__ __forceinline__ double finish_row(const double* __restrict__ partial, int k, int lane) {
+    double s = 0.0;
+    for (int b = lane; b < kDotBlocks; b += 32) s += partial[(int64_t)k * kDotBlocks + b];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    return s;
+}
+
+// Every block publishes its partials; the last block to finish (ticket) sums
+// them in the fixed order above.  Returns true in the last block.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = t == gridDim.x - 1;
+        if (s_last) atomicExch(counter, 0u);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+// out[k] = V_k . w for k < nvec, in one launch.
+__global__ void __launch_bounds__(kThreads)
+k_multidot_fused(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w, int64_t n,
+                 double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
+    NMG_PDL_ENTRY();
+    __shared__ double red[kThreads / 32];
+    for (int kc = 0; kc < nvec; kc += kChunk) {
+        double acc[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
+            const double wi = w[i];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q)
+                if (kc + q < nvec) acc[q] = fma(V[(int64_t)(kc + q) * ldv + i], wi, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            if (kc + q >= nvec) break;
+            const double s = block_sum(acc[q], red);
+            if (threadIdx.x == 0) partial[(int64_t)(kc + q) * kDotBlocks + blockIdx.x] = s;
+        }
+    }
+    if (!last_block(counter)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < nvec; k += kThreads / 32) {
+        const double s = finish_row(partial, k, lane);
+        if (lane == 0) out[k] = s;
+    }
+}
+
+// Second Gram-Schmidt pass w -= sum h_k V_k, ||w|| into scal[S_HC + j + 1], then
+// the Givens update of Hessenberg column j, in one launch.
+__global__ void __launch_bounds__(kThreads)
+k_gs_norm_arnoldi(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
+                  double* __restrict__ w, int64_t n, double* __restrict__ partial, double* scal, int j, int m,
+                  unsigned* counter) {
+    NMG_PDL_ENTRY();
+    __shared__ double red[kThreads / 32];
+    __shared__ double hs[kMaxRestart + 1];
+    for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
+    __syncthreads();
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
+        double v = w[i];
+        for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
+        w[i] = v;
+        acc = fma(v, v, acc);
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (!last_block(counter)) return;
+    if (threadIdx.x < 32) {
+        const double t = finish_row(partial, 0, threadIdx.x);
+        if (threadIdx.x == 0) {
+            scal[S_HC + j + 1] = sqrt(t);
+            arnoldi_column(scal, j, m);
+        }
+    }
+}
+
+// y = x * scal[S_INVH] (the next Krylov vector) and, when y32 is given, its
+// FP32 copy (the right-hand side of the next reduced-precision V-cycle).
+__global__ void k_scale_convert(const double* __restrict__ x, const double* __restrict__ sp, double* __restrict__ y,
+                                float* __restrict__ y32, int64_t n) {
+    NMG_PDL_ENTRY();
+    const double a = *sp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = a * x[i];
+        y[i] = v;
+        if (y32) y32[i] = (float)v;
+    }
+}
+
 }  // namespace
 
 void launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t s) {
@@ -234,6 +338,29 @@ void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ld
 void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s) {
     g_launches += 1;
     pdl_launch(k_axpby, dim3(grid_for(n)), dim3(256), 0, s, a, x, b, y, n);
+}
+
+}  // namespace nmg
+
+namespace nmg {
+
+void launch_multidot_fused(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
+                           double* out, unsigned* counter, cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_multidot_fused, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, w, n, partial, out, counter);
+}
+
+void launch_gs_norm_arnoldi(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
+                            double* partial, double* scal, int j, int m, unsigned* counter, cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_gs_norm_arnoldi, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, h, w, n, partial, scal, j,
+               m, counter);
+}
+
+void launch_scale_convert(const double* x, const double* scal_ptr, double* y, float* y32, int64_t n,
+                          cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_scale_convert, dim3(grid_for(n)), dim3(256), 0, s, x, scal_ptr, y, y32, n);
 }
 
 }  // namespace nmg

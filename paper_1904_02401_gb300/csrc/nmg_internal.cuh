@@ -49,6 +49,7 @@ struct PrecData {                 // per-precision data of one level
     void* x = nullptr;
     void* r = nullptr;
     void* corr = nullptr;         // per-patch corrections A_i^{-1} R_i d, patches * n_p
+    void* x2 = nullptr;           // second iterate buffer of the fused V-cycle (ping-pong with x)
 };
 
 struct Level {
@@ -95,12 +96,14 @@ struct Hierarchy {
     int64_t vgraph_nodes[3] = {0, 0, 0};
     // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
     unsigned* pbar = nullptr;
+    unsigned* counters = nullptr;        // last-block tickets of the fused reductions
     int engine_choice[3] = {0, 0, 0};
+    int fused[3] = {0, 0, 0};            // per-step engine: fused update/prolongation + residual kernels
     int tail_patches[3] = {0, 0, 0};     // levels with at most this many patches run in the one-CTA tail
                                          // (0: none; the autotuner may pick a threshold)
     int engine_key[3][3] = {};
     double engine_us[3][2] = {};
-    struct Trial { int engine, tail; double us; };
+    struct Trial { int engine, tail, fused; double us; };
     std::vector<Trial> tuning;             // the autotuner's last measurements
     double prof_bytes = 0.0;
     std::vector<void*> allocs;
@@ -142,6 +145,16 @@ template <typename T>
 void launch_vanka_update(const Geom& g, const T* corr, T* x, bool x_zero, T omega, bool average,
                          cudaStream_t s);
 template <typename T>
+void launch_vanka_update2(const Geom& g, const T* corr, const T* x_in, T* x_out, bool x_zero, T omega, bool average,
+                          cudaStream_t s);
+// fused forms of the V-cycle (same element code as the separate kernels)
+template <typename T>
+void launch_update_residual(const Geom& g, const T* A, const T* corr, const T* x_in, bool x_zero, T omega,
+                            bool average, const T* b, T* x_out, T* r, cudaStream_t s);
+template <typename T>
+void launch_prolong_residual(const Geom& f, const Geom& c, const T* A, const T* ec, const T* x_in,
+                             const uint8_t* fmask, const T* b, T* x_out, T* r, cudaStream_t s);
+template <typename T>
 void launch_restrict(const Geom& fine, const Geom& coarse, const T* rf, T* rc,
                      const uint8_t* cmask, cudaStream_t s);
 template <typename T>
@@ -178,6 +191,15 @@ void launch_start_cycle(double* scal, int m, cudaStream_t s);
 void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x,
                          int64_t n, cudaStream_t s);
 void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
+// fused forms used by the solve (same summation orders as the separate kernels)
+void launch_multidot_fused(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
+                           double* out, unsigned* counter, cudaStream_t s);
+void launch_gs_norm_arnoldi(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
+                            double* partial, double* scal, int j, int m, unsigned* counter, cudaStream_t s);
+void launch_scale_convert(const double* x, const double* scal_ptr, double* y, float* y32, int64_t n,
+                          cudaStream_t s);
+template <typename TX>
+void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* z64, double* w, cudaStream_t s);
 
 }  // namespace nmg
 

@@ -228,7 +228,7 @@ struct VCycle {
             phase(a, cx, L.small, [&] {
                 const Range r = threads(L.small);
                 for (int64_t i = r.first; i < L.g.nodes; i += r.step)
-                    vanka_update_node<T, DIM>(L.g, (const T*)L.corr, (T*)L.x, first, om, a.average != 0, i);
+                    vanka_update_node<T, DIM>(L.g, (const T*)L.corr, (const T*)L.x, (T*)L.x, first, om, a.average != 0, i);
             });
         }
     }

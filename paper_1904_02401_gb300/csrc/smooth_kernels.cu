@@ -28,6 +28,22 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
     if (i < g.nodes) spmv_node<T, DIM>(g, A, x, b, y, residual, i);
 }
 
+// w = A z in FP64 with z read from the V-cycle output xf (stored as TX) and
+// written, converted, to z64 (the FGMRES basis vector Z_j): the outer product
+// of one FGMRES iteration without a separate conversion pass.
+template <typename TX, int DIM>
+__global__ void __launch_bounds__(256)
+k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ z64,
+              double* __restrict__ w) {
+    NMG_PDL_ENTRY();
+    constexpr int NC = DIM + 1;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.nodes) return;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z64[i * NC + c] = (double)xf[i * NC + c];
+    spmv_node<double, DIM, TX>(g, A, xf, nullptr, w, false, i);
+}
+
 // corr_i = A_i^{-1} R_i d for every patch i: one warp per patch.  The patch
 // inverse is column-major, so for each column j the 32 lanes read 32
 // consecutive entries (one coalesced 128-byte segment in FP32) and multiply
@@ -92,11 +108,34 @@ k_vanka_apply_staged2d(Geom g, const TS* __restrict__ inv, int64_t stride, const
 // ("average") or omega ("sum").  One thread per node, no atomics.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256)
-k_vanka_update(Geom g, const T* __restrict__ corr, T* __restrict__ x, bool x_zero, T omega,
+k_vanka_update(Geom g, const T* __restrict__ corr, const T* x_in, T* x_out, bool x_zero, T omega,
                bool average) {
     NMG_PDL_ENTRY();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < g.nodes) vanka_update_node<T, DIM>(g, corr, x, x_zero, omega, average, i);
+    if (i < g.nodes) vanka_update_node<T, DIM>(g, corr, x_in, x_out, x_zero, omega, average, i);
+}
+
+// Fused Vanka update and residual: x_out = x_in + w * corrections, r = b - A x_out
+// (x_out at the neighbours recomputed from x_in and the corrections).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256)
+k_update_residual(Geom g, const T* __restrict__ A, const T* __restrict__ corr, const T* __restrict__ x_in,
+                  bool x_zero, T omega, bool average, const T* __restrict__ b, T* __restrict__ x_out,
+                  T* __restrict__ r) {
+    NMG_PDL_ENTRY();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < g.nodes) update_residual_node<T, DIM>(g, A, corr, x_in, x_zero, omega, average, b, x_out, r, i);
+}
+
+// Fused prolongation and residual: x_out = x_in + P e_c, r = b - A x_out.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256)
+k_prolong_residual(Geom f, Geom c, const T* __restrict__ A, const T* __restrict__ ec, const T* __restrict__ x_in,
+                   const uint8_t* __restrict__ fmask, const T* __restrict__ b, T* __restrict__ x_out,
+                   T* __restrict__ r) {
+    NMG_PDL_ENTRY();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < f.nodes) prolong_residual_node<T, DIM>(f, c, A, ec, x_in, fmask, b, x_out, r, i);
 }
 
 // r_c = P^T r_f (Q1 full weighting), coarse Dirichlet entries zero.  One thread per coarse node.
@@ -165,6 +204,16 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
     else pdl_launch(k_spmv<T, 3>, grid, dim3(256), 0, s, g, A, x, b, y, residual);
 }
 
+template <typename TX>
+void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* z64, double* w, cudaStream_t s) {
+    g_launches += 1;
+    const dim3 grid(blocks_for(g.nodes, 256));
+    if (g.dim == 2) pdl_launch(k_spmv_zstore<TX, 2>, grid, dim3(256), 0, s, g, A, xf, z64, w);
+    else pdl_launch(k_spmv_zstore<TX, 3>, grid, dim3(256), 0, s, g, A, xf, z64, w);
+}
+template void launch_spmv_zstore<float>(const Geom&, const double*, const float*, double*, double*, cudaStream_t);
+template void launch_spmv_zstore<double>(const Geom&, const double*, const double*, double*, double*, cudaStream_t);
+
 template <typename T, typename TS>
 void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
     g_launches += 1;
@@ -191,11 +240,50 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
 
 template <typename T>
 void launch_vanka_update(const Geom& g, const T* corr, T* x, bool x_zero, T omega, bool average, cudaStream_t s) {
+    launch_vanka_update2<T>(g, corr, x, x, x_zero, omega, average, s);
+}
+
+template <typename T>
+void launch_vanka_update2(const Geom& g, const T* corr, const T* x_in, T* x_out, bool x_zero, T omega, bool average,
+                          cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(g.nodes, 256));
-    if (g.dim == 2) pdl_launch(k_vanka_update<T, 2>, grid, dim3(256), 0, s, g, corr, x, x_zero, omega, average);
-    else pdl_launch(k_vanka_update<T, 3>, grid, dim3(256), 0, s, g, corr, x, x_zero, omega, average);
+    if (g.dim == 2) pdl_launch(k_vanka_update<T, 2>, grid, dim3(256), 0, s, g, corr, x_in, x_out, x_zero, omega, average);
+    else pdl_launch(k_vanka_update<T, 3>, grid, dim3(256), 0, s, g, corr, x_in, x_out, x_zero, omega, average);
 }
+
+template <typename T>
+void launch_update_residual(const Geom& g, const T* A, const T* corr, const T* x_in, bool x_zero, T omega,
+                            bool average, const T* b, T* x_out, T* r, cudaStream_t s) {
+    g_launches += 1;
+    const dim3 grid(blocks_for(g.nodes, 256));
+    if (g.dim == 2)
+        pdl_launch(k_update_residual<T, 2>, grid, dim3(256), 0, s, g, A, corr, x_in, x_zero, omega, average, b, x_out, r);
+    else
+        pdl_launch(k_update_residual<T, 3>, grid, dim3(256), 0, s, g, A, corr, x_in, x_zero, omega, average, b, x_out, r);
+}
+
+template <typename T>
+void launch_prolong_residual(const Geom& f, const Geom& c, const T* A, const T* ec, const T* x_in,
+                             const uint8_t* fmask, const T* b, T* x_out, T* r, cudaStream_t s) {
+    g_launches += 1;
+    const dim3 grid(blocks_for(f.nodes, 256));
+    if (f.dim == 2) pdl_launch(k_prolong_residual<T, 2>, grid, dim3(256), 0, s, f, c, A, ec, x_in, fmask, b, x_out, r);
+    else pdl_launch(k_prolong_residual<T, 3>, grid, dim3(256), 0, s, f, c, A, ec, x_in, fmask, b, x_out, r);
+}
+
+template void launch_vanka_update2<double>(const Geom&, const double*, const double*, double*, bool, double, bool,
+                                           cudaStream_t);
+template void launch_vanka_update2<float>(const Geom&, const float*, const float*, float*, bool, float, bool,
+                                          cudaStream_t);
+template void launch_update_residual<double>(const Geom&, const double*, const double*, const double*, bool, double,
+                                             bool, const double*, double*, double*, cudaStream_t);
+template void launch_update_residual<float>(const Geom&, const float*, const float*, const float*, bool, float, bool,
+                                            const float*, float*, float*, cudaStream_t);
+template void launch_prolong_residual<double>(const Geom&, const Geom&, const double*, const double*, const double*,
+                                              const uint8_t*, const double*, double*, double*, cudaStream_t);
+template void launch_prolong_residual<float>(const Geom&, const Geom&, const float*, const float*, const float*,
+                                             const uint8_t*, const float*, float*, float*, cudaStream_t);
 
 template <typename T>
 void launch_restrict(const Geom& f, const Geom& c, const T* rf, T* rc, const uint8_t* cmask, cudaStream_t s) {

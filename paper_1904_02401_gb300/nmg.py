@@ -36,6 +36,7 @@ NMG_WEIGHT_SUM = 1
 NMG_ENGINE_AUTO = 0
 NMG_ENGINE_KERNELS = 1
 NMG_ENGINE_PERSISTENT = 2
+NMG_ENGINE_FUSED = 3
 
 
 class nmg_mesh_desc(C.Structure):

@@ -189,7 +189,7 @@ def test_transfers_and_coarse(nmg, built, sessions, case, prec):
 
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("engine,use_graph", [(1, 0), (1, 1), (2, 0)])
+@pytest.mark.parametrize("engine,use_graph", [(1, 0), (1, 1), (2, 0), (3, 0), (3, 1)])
 def test_vcycle(nmg, built, sessions, case, prec, engine, use_graph):
     from paper_1904_02401_gb300.session import solve_opts
     s, h = built[case]
@@ -310,20 +310,21 @@ def test_error_paths(nmg, built):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", PRECS)
 def test_engines_agree(nmg, built, sessions, case, prec):
-    """One-kernel-per-step (plain and graph) and persistent V-cycles run the same
-    element code in the same order: their results are bitwise identical."""
+    """One-kernel-per-step (plain and graph), fused and persistent V-cycles run the
+    same element code in the same order: their results are bitwise identical."""
     from paper_1904_02401_gb300.session import solve_opts
     s, h = built[case]
     S = sessions[case]
     dt = vdtype(prec)
     r = cu(s.rhs.astype(dt), dt)
     outs = []
-    for engine, graph in ((nmg.NMG_ENGINE_KERNELS, 0), (nmg.NMG_ENGINE_KERNELS, 1), (nmg.NMG_ENGINE_PERSISTENT, 0)):
+    for engine, graph in ((nmg.NMG_ENGINE_KERNELS, 0), (nmg.NMG_ENGINE_KERNELS, 1), (nmg.NMG_ENGINE_PERSISTENT, 0),
+                          (nmg.NMG_ENGINE_FUSED, 0), (nmg.NMG_ENGINE_FUSED, 1)):
         z = torch.zeros_like(r)
         nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=graph, engine=engine), r, z))
         outs.append(z)
-    assert torch.equal(outs[0], outs[1])
-    assert torch.equal(outs[0], outs[2])
+    for k in range(1, len(outs)):
+        assert torch.equal(outs[0], outs[k]), k
 
 
 @pytest.mark.parametrize("case", list(CASES))
