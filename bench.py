@@ -37,6 +37,13 @@ WORKLOADS = {
     "cfg4": ("3d 96^3 Q1 condensed-momentum Jacobian (3,650,692 unknowns), solid z<0.25, "
              "6 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
 }
+# DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
+# capture of the current kernel source (profiles/k_vanka_apply_*.md); a
+# workload or precision without a capture of the current source reports null.
+PROFILED_TRAFFIC = {
+    ("cfg2", 1): 48_784_896 + 26_880,       # k_vanka_apply_staged2d, 2d 256x256, FP32
+    ("cfg3", 1): 191_955_712 + 3_209_728,   # k_vanka_apply<float,float,3,4>, 3d 32^3, FP32
+}
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 
@@ -327,7 +334,8 @@ def gpu_arm(args):
         "roofline": {"kernel": ("k_vanka_apply_staged2d" if sysm.problem.dim == 2 else "k_vanka_apply") +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": PROFILED_TRAFFIC.get((WORKLOAD, args.precision)),
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
                      "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
