@@ -55,13 +55,18 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nmg", choices=["nmg", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="V-cycle precision: 0 FP64, 1 FP32, 2 BF16")
-    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="plain launches, host-stepped FGMRES (use_graph 0)")
+    ap.add_argument("--graph", type=int, default=2, choices=[0, 1, 2],
+                    help="1: V-cycle graphs with host-stepped FGMRES; 2: also one on-device loop per restart cycle")
     ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent", "fused"],
                     help="V-cycle engine (auto: the autotuner picks it on the first solve)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true",
                     help="serving workload: Poisson stream of solves over resident 2d/3d hierarchies")
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="after the warm-up, run one solve between cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off) and exit")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS),
                     help="cfg2 is the measured workload; the others are for investigation")
     return ap.parse_args()
@@ -224,7 +229,7 @@ def gpu_arm(args):
     b = torch.from_numpy(sysm.rhs).cuda()
     x = torch.empty_like(b)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    use_graph = 0 if args.no_graph else 1
+    use_graph = 0 if args.no_graph else args.graph
     engine = {"auto": nmg.NMG_ENGINE_AUTO, "kernels": nmg.NMG_ENGINE_KERNELS,
               "persistent": nmg.NMG_ENGINE_PERSISTENT, "fused": nmg.NMG_ENGINE_FUSED}[args.engine]
 
@@ -254,6 +259,17 @@ def gpu_arm(args):
 
     # warm-up (also captures the V-cycle graphs)
     timed_solves(args.precision, args.warmup, use_graph)
+    if args.profile_range:
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            info = S.solve(b, x, precision=args.precision, use_graph=use_graph, engine=engine)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profile_range": WORKLOAD, "iterations": info.iterations, "launches": info.launches,
+                              "status": info.status}), flush=True)
+        return
     timed_solves(nmg.NMG_PREC_FP64, max(1, args.warmup // 2), use_graph)
 
     clocks = ClockSampler(local)
@@ -272,7 +288,7 @@ def gpu_arm(args):
     # the dominant kernel (finest-level Vanka apply) timed per launch with events on its launch
     # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
     ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
-    _, _, vprof = timed_solves(args.precision, args.steps, use_graph, profile=1)
+    _, _, vprof = timed_solves(args.precision, args.steps, min(use_graph, 1), profile=1)
     rep = C.create_string_buffer(8192)
     nmg.check(nmg.nmg_autotune_report(S.handle, rep, 8192))
     # plain FP64 path on the same mesh
@@ -320,7 +336,11 @@ def gpu_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "unknowns": n, "levels": sysm.problem.levels,
                    "vcycle_precision": {0: "fp64", 1: "fp32", 2: "bf16 factors"}[args.precision],
-                   "outer": "fp64 FGMRES(30)", "cuda_graph": bool(use_graph),
+                   "outer": "fp64 FGMRES(30)",
+                   "graphs": {0: "none (plain launches, host-stepped FGMRES)",
+                              1: "V-cycle graph, host-stepped FGMRES",
+                              2: "V-cycle inside one on-device graph loop per FGMRES restart cycle"}[use_graph],
+                   "device_loop": bool(infos[-1].device_loop),
                    "l2": "flushed before every solve (256 MB write, outside the per-solve events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iterations": infos[-1].iterations,

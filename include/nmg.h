@@ -89,8 +89,15 @@ typedef struct {
     double omega;     /* Vanka damping omega_V (Section 4.3: about 0.8)                           */
     int precision;    /* NMG_PREC_* of the V-cycle; must be among the prepared precisions          */
     int weighting;    /* NMG_WEIGHT_*                                                             */
-    int use_graph;    /* 1: replay the V-cycle as a captured CUDA graph; 0: plain launches        */
+    int use_graph;    /* 0: plain launches, the host decides after every FGMRES step;
+                         1: the V-cycle replayed as a captured CUDA graph, host-stepped;
+                         2: as 1, and the steps of each restart cycle run as one graph with an
+                            on-device loop (one host round trip per cycle); falls back to 1 where
+                            the driver cannot build it or the engine is PERSISTENT            */
     int engine;       /* NMG_ENGINE_*: how a V-cycle is executed                                  */
+    int tail_patches; /* engines KERNELS and FUSED: the coarse level and every level with at most
+                         this many patches run as one thread-block-cluster kernel (0 = none);
+                         AUTO picks it itself, PERSISTENT ignores it                              */
 } nmg_solve_opts;
 
 /* V-cycle execution engines (same arithmetic, same results). */
@@ -108,11 +115,12 @@ typedef struct {
     double ms_total;      /* wall time of the call, milliseconds                           */
     nmg_status status;    /* status of the solve (also the return value)                  */
     int64_t launches;     /* CUDA kernels this solve launched (graph nodes counted each replay) */
-    int engine;           /* NMG_ENGINE_KERNELS or NMG_ENGINE_PERSISTENT, the engine used     */
+    int engine;           /* NMG_ENGINE_KERNELS, _PERSISTENT or _FUSED, the engine used       */
+    int device_loop;      /* 1 when restart cycles ran as graph loops on the device          */
 } nmg_solve_info;
 
 /* Fills *opts with rtol 1e-8, restart 30, maxit 1000, nu1 = nu2 = 2, omega 0.8,
- * precision FP32, weighting AVERAGE, use_graph 1, engine AUTO. */
+ * precision FP32, weighting AVERAGE, use_graph 2, engine AUTO, tail_patches 0. */
 nmg_status nmg_default_opts(nmg_solve_opts* opts);
 
 /* Creates an empty hierarchy for the mesh in *desc (Section 4.3 (II): nested
@@ -212,9 +220,12 @@ nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* 
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int precision, int64_t first,
                                   int64_t count, double* out);
 
-/* The V-cycle autotuner's choices (engine and one-CTA tail threshold per
- * precision) and its last trial timings, as a NUL-terminated JSON object in
- * buf (len bytes).  NMG_ERR_INVALID if buf is too small. */
+/* The V-cycle autotuner's choices (engine and cluster-tail threshold per
+ * precision), its last trial timings and the state of the on-device FGMRES
+ * loop (mode 0 not built yet, 1 built with programmatic launch edges, 2 built
+ * without them, -1 unavailable; kernels per loop step per precision), as a
+ * NUL-terminated JSON object in buf (len bytes).  NMG_ERR_INVALID if buf is
+ * too small. */
 nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len);
 
 /* Bytes of device memory held by the hierarchy. */

@@ -21,6 +21,7 @@ namespace nmg {
 
 thread_local std::string g_last_error = "no error";
 thread_local int64_t g_launches = 0;
+thread_local bool g_no_pdl = false;
 
 static nmg_status fail(nmg_status st, const std::string& msg) {
     g_last_error = msg;
@@ -164,7 +165,7 @@ static void run_vcycle(Hierarchy* h, int prec, int nu1, int nu2, double omega, i
     const T om = (T)omega;
     auto bptr = [&](int l) -> T* { return (l == Lc - 1 && b_fine) ? const_cast<T*>(b_fine) : (T*)h->lev[l].p[prec].b; };
     auto xptr = [&](int l) -> T* { return (l == Lc - 1 && x_fine) ? x_fine : (T*)h->lev[l].p[prec].x; };
-    // levels 0..c (all with at most tail_patches patches) run as one single-CTA kernel
+    // levels 0..c (all with at most tail_patches patches) run as one cluster kernel
     int c = -1;
     if (h->tail_patches[prec] > 0)
         for (int l = 0; l < Lc && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
@@ -324,8 +325,8 @@ static nmg_status validate_opts(const nmg_solve_opts* o) {
     if (!o) return fail(NMG_ERR_INVALID, "opts is NULL");
     if (!(o->rtol >= 0.0) || o->restart < 1 || o->restart > kMaxRestart || o->maxit < 0 || o->nu1 < 0 ||
         o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64 || !std::isfinite(o->omega) ||
-        (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM) ||
-        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_FUSED)
+        (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM) || o->use_graph < 0 || o->use_graph > 2 ||
+        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_FUSED || o->tail_patches < 0)
         return fail(NMG_ERR_INVALID, "invalid solve options");
     return NMG_OK;
 }
@@ -372,17 +373,20 @@ static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) 
 
 // Autotuner.  For AUTO the V-cycle shape is picked by timing the candidates
 // on this hierarchy (finest right-hand side zeroed, so the memory traffic is
-// the real one): the per-step-kernel engine with the one-CTA tail covering
-// levels of at most {0, 16, 64, 256, 1024} patches, and the persistent engine.
+// the real one): the per-step-kernel engine, plain or with fused
+// update/prolongation + residual, with the cluster tail covering the levels of
+// at most {0, 64, 256, 1024, 4096} patches, and the persistent engine.
 // The fastest is kept per precision and (nu1, nu2, weighting).
 static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* engine) {
+    const int prec = o.precision;
     if (o.engine != NMG_ENGINE_AUTO) {
+        h->tail_patches[prec] = o.engine == NMG_ENGINE_PERSISTENT ? 0 : o.tail_patches;
         *engine = o.engine;
         return NMG_OK;
     }
-    const int prec = o.precision;
     const int key[3] = {o.nu1, o.nu2, o.weighting};
     if (h->engine_choice[prec] && std::memcmp(key, h->engine_key[prec], sizeof(key)) == 0) {
+        h->tail_patches[prec] = h->auto_tail[prec];
         *engine = h->engine_choice[prec];
         return NMG_OK;
     }
@@ -395,7 +399,7 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     struct Cand { int engine, tail, fused; };
     std::vector<Cand> cands;
     int last_level = -2;
-    for (int tail : {0, 16, 64}) {
+    for (int tail : {0, 64, 256, 1024, 4096}) {
         int c = -1;
         if (tail > 0)
             for (int l = 0; l < h->L && (l == 0 || h->lev[l].g.patches <= tail); ++l) c = l;
@@ -437,6 +441,7 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     }
     h->fused[prec] = pick.fused;
     h->tail_patches[prec] = pick.tail;
+    h->auto_tail[prec] = pick.tail;
     h->engine_choice[prec] = pick.engine;
     std::memcpy(h->engine_key[prec], key, sizeof(key));
     *engine = pick.engine;
@@ -461,17 +466,18 @@ static nmg_status vcycle_in_place(Hierarchy* h, const nmg_solve_opts& o) {
     return NMG_OK;
 }
 
-// v = w * scal[S_INVH] (the next FP64 Krylov vector), also written as the
-// right-hand side of the next V-cycle (converted for reduced precision).
-static cudaError_t scale_into_vcycle_input(Hierarchy* h, const nmg_solve_opts& o, const double* w, double* v) {
+// v = w * scal[S_INVH] into the Krylov basis (column j + 1 of the current
+// step when next, else column 0), also written, converted, as the right-hand
+// side of the next V-cycle.
+static void scale_into_vcycle_input(Hierarchy* h, const nmg_solve_opts& o, const double* w, bool next) {
     Level& F = h->lev[h->L - 1];
     const int64_t n = F.g.nodes * F.g.nc;
-    if (o.precision == NMG_PREC_FP64) {
-        launch_scale_convert(w, h->scal + S_INVH, v, nullptr, n, h->stream);
-        return cudaMemcpyAsync(F.p[NMG_PREC_FP64].b, v, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
-    }
-    launch_scale_convert(w, h->scal + S_INVH, v, (float*)F.p[o.precision].b, n, h->stream);
-    return cudaGetLastError();
+    if (o.precision == NMG_PREC_FP64)
+        launch_scale_convert<double>(w, h->scal + S_INVH, h->V, n, h->cyc, next, (double*)F.p[NMG_PREC_FP64].b, n,
+                                     h->stream);
+    else
+        launch_scale_convert<float>(w, h->scal + S_INVH, h->V, n, h->cyc, next, (float*)F.p[o.precision].b, n,
+                                    h->stream);
 }
 
 // z = V-cycle(v) for vectors of the precision's arithmetic type or FP64 (converted).
@@ -522,6 +528,7 @@ static nmg_status ensure_krylov(Hierarchy* h, int m) {
     NMG_TRY(dalloc(h, (void**)&h->V, (size_t)(m + 1) * n * sizeof(double)));
     NMG_TRY(dalloc(h, (void**)&h->Z, (size_t)m * n * sizeof(double)));
     h->m_alloc = m;
+    h->krylov_gen++;
     return NMG_OK;
 }
 
@@ -536,13 +543,15 @@ static bool is_device_ptr(const void* p) {
 
 struct SolveJob {
     enum Phase { P_NONE, P_NORM, P_CYCLE, P_ITER, P_FINISH, P_DONE };
+    bool loop = false;        // the current cycle's steps were enqueued as one graph loop
     Hierarchy* h = nullptr;
     nmg_solve_opts o{};
     const double* b_user = nullptr;
     double* x_user = nullptr;
     bool b_dev = false, x_dev = false;
     Phase phase = P_NONE;
-    int j = 0, its = 0, cycles = 0, engine = NMG_ENGINE_KERNELS;
+    int its = 0, cycles = 0, engine = NMG_ENGINE_KERNELS;
+    bool used_loop = false;
     double bnorm = 0.0, relres = 0.0;
     nmg_status st = NMG_OK;
     std::string err;
@@ -581,40 +590,130 @@ static void job_enqueue_cycle(SolveJob& J) {
     // true residual r = b - A x and beta = ||r||, v_0 = r / beta
     launch_spmv<double>(g, h->lev[h->L - 1].A64, h->x64, h->b64, h->w64, true, s);
     launch_norm2(h->w64, n, h->partial, h->scal + S_BETA, s);
-    launch_start_cycle(h->scal, J.o.restart, s);
-    JOB_CK(scale_into_vcycle_input(h, J.o, h->w64, h->V));
+    launch_start_cycle(h->scal, J.o.restart, h->cyc, s);
+    scale_into_vcycle_input(h, J.o, h->w64, false);
     JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     J.phase = SolveJob::P_CYCLE;
 }
 
-static void job_enqueue_iter(SolveJob& J) {
-    Hierarchy* h = J.h;
+// One FGMRES step j (read on the device from cyc[0]): z_j = M^{-1} v_j (v_j is
+// already the V-cycle's right-hand side, written by the scaling that produced
+// it), w = A z_j in FP64 with z_j stored as basis vector Z_j, two classical
+// Gram-Schmidt passes (the second ends with ||w|| and the Givens update),
+// v_{j+1} = w / h_{j+1,j}, and the on-device decision whether the cycle goes
+// on.  in_loop: the launches are being captured as the body of a graph loop
+// whose condition the decision sets (the V-cycle is captured inline then).
+static nmg_status enqueue_step(Hierarchy* h, const nmg_solve_opts& o, int engine, bool in_loop,
+                               cudaGraphConditionalHandle loop) {
     const Geom& g = h->lev[h->L - 1].g;
     const int64_t n = g.nodes * g.nc;
-    const int j = J.j, m = J.o.restart;
+    const int m = o.restart;
     cudaStream_t s = h->stream;
-    double* zj = h->Z + (int64_t)j * n;
-    // z_j = M^{-1} v_j: v_j is already the V-cycle's right-hand side (written by
-    // the scaling that produced it), the result stays in the level buffer
-    const nmg_status st = vcycle_in_place(h, J.o);
-    if (st != NMG_OK) {
-        job_fail(J, st);
-        J.phase = SolveJob::P_DONE;
-        return;
+    if (in_loop) {
+        h->fused[o.precision] = engine == NMG_ENGINE_FUSED;
+        vcycle_dispatch(h, o.precision, o, nullptr, nullptr);
+    } else {
+        NMG_TRY(vcycle_in_place(h, o));
     }
-    const PrecData& PF = h->lev[h->L - 1].p[J.o.precision];
+    const PrecData& PF = h->lev[h->L - 1].p[o.precision];
     double* A64 = h->lev[h->L - 1].A64;
-    // w = A z_j (FP64), z_j stored as basis vector Z_j
-    if (J.o.precision == NMG_PREC_FP64) launch_spmv_zstore<double>(g, A64, (const double*)PF.x, zj, h->w64, s);
-    else launch_spmv_zstore<float>(g, A64, (const float*)PF.x, zj, h->w64, s);
-    // classical Gram-Schmidt, two passes; the second ends with ||w|| and the Givens update
-    launch_multidot_fused(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_HC, h->counters, s);
-    launch_gs_update(h->V, n, j + 1, h->scal + S_HC, h->w64, n, h->partial, nullptr, false, s);
-    launch_multidot_fused(h->V, n, j + 1, h->w64, n, h->partial, h->scal + S_Y, h->counters, s);
-    launch_gs_norm_arnoldi(h->V, n, j + 1, h->scal + S_Y, h->w64, n, h->partial, h->scal, j, m, h->counters, s);
-    // v_{j+1} = w / h_{j+1,j}, also written as the next V-cycle's right-hand side
-    JOB_CK(scale_into_vcycle_input(h, J.o, h->w64, h->V + (int64_t)(j + 1) * n));
+    if (o.precision == NMG_PREC_FP64) launch_spmv_zstore<double>(g, A64, (const double*)PF.x, h->Z, n, h->cyc, h->w64, s);
+    else launch_spmv_zstore<float>(g, A64, (const float*)PF.x, h->Z, n, h->cyc, h->w64, s);
+    launch_multidot_fused(h->V, n, h->cyc, h->w64, n, h->partial, h->scal + S_HC, h->counters, s);
+    launch_gs_update_dot(h->V, n, h->cyc, h->scal + S_HC, h->w64, n, h->partial, h->scal + S_Y, h->counters, s);
+    launch_gs_norm_arnoldi(h->V, n, h->scal + S_Y, h->w64, n, h->partial, h->scal, h->cyc, m, h->counters, s);
+    scale_into_vcycle_input(h, o, h->w64, true);
+    launch_decide(h->scal, h->cyc, o.rtol, o.maxit, m, loop, in_loop, s);
+    return NMG_OK;
+}
+
+// The steps of one restart cycle as one executable graph: a while-loop node
+// whose body is enqueue_step and whose condition the step's decision kernel
+// sets, so a cycle needs no host round trip per step.  Built once per
+// (precision, options, engine) and replayed; nullptr when the device or the
+// driver cannot build it (the host then steps the cycle).
+static cudaGraphExec_t cycle_graph(Hierarchy* h, const nmg_solve_opts& o, int engine) {
+    if (h->loop_mode < 0 || engine == NMG_ENGINE_PERSISTENT) return nullptr;
+    const int prec = o.precision;
+    Hierarchy::LoopKey key{};
+    key.nu1 = o.nu1; key.nu2 = o.nu2; key.weighting = o.weighting; key.engine = engine;
+    key.tail = h->tail_patches[prec]; key.restart = o.restart; key.maxit = o.maxit; key.gen = h->krylov_gen;
+    key.omega = o.omega; key.rtol = o.rtol;
+    const Hierarchy::LoopKey& k0 = h->cgraph_key[prec];
+    if (h->cgraph[prec] && k0.nu1 == key.nu1 && k0.nu2 == key.nu2 && k0.weighting == key.weighting &&
+        k0.engine == key.engine && k0.tail == key.tail && k0.restart == key.restart && k0.maxit == key.maxit &&
+        k0.gen == key.gen && k0.omega == key.omega && k0.rtol == key.rtol)
+        return h->cgraph[prec];
+    if (h->cgraph[prec]) cudaGraphExecDestroy(h->cgraph[prec]);
+    h->cgraph[prec] = nullptr;
+    // first with programmatic launch edges inside the body, then without
+    for (int mode = h->loop_mode == 2 ? 2 : 1; mode <= 2; ++mode) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+        cudaGraphConditionalHandle cond = 0;
+        ok = ok && cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = cond;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = ok && cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t body = p.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                cudaSuccess) {
+                const int prof = h->prof;
+                h->prof = 0;
+                g_no_pdl = mode == 2;
+                const int64_t before = g_launches;
+                const nmg_status st = enqueue_step(h, o, engine, true, cond);
+                h->cgraph_nodes[prec] = g_launches - before;
+                g_launches = before;
+                g_no_pdl = false;
+                h->prof = prof;
+                const cudaError_t e = cudaStreamEndCapture(h->stream, &body);
+                ok = st == NMG_OK && e == cudaSuccess;
+            } else {
+                ok = false;
+            }
+        }
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (ok) {
+            h->loop_mode = mode;
+            h->cgraph[prec] = exec;
+            h->cgraph_key[prec] = key;
+            return exec;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    h->loop_mode = -1;
+    return nullptr;
+}
+
+// Enqueues the steps of the current cycle: all of them as one graph loop
+// (use_graph 2), or the next single step (the host decides after each).
+static void job_enqueue_iter(SolveJob& J) {
+    Hierarchy* h = J.h;
+    cudaStream_t s = h->stream;
+    cudaGraphExec_t loop = J.o.use_graph == 2 ? cycle_graph(h, J.o, J.engine) : nullptr;
+    J.loop = loop != nullptr;
+    if (loop) {
+        J.used_loop = true;
+        JOB_CK(cudaGraphLaunch(loop, s));
+    } else {
+        const nmg_status st = enqueue_step(h, J.o, J.engine, false, 0);
+        if (st != NMG_OK) {
+            job_fail(J, st);
+            J.phase = SolveJob::P_DONE;
+            return;
+        }
+    }
     JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    JOB_CK(cudaMemcpyAsync(h->host_cyc, h->cyc, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     J.phase = SolveJob::P_ITER;
 }
 
@@ -651,6 +750,7 @@ static nmg_status job_start(SolveJob& J, Hierarchy* h, const double* b_user, dou
     NMG_CK(cudaMemcpyAsync(h->b64, b_user, n * sizeof(double), J.b_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     NMG_CK(cudaMemsetAsync(h->scal, 0, 8 * sizeof(double), s));
     NMG_CK(cudaMemsetAsync(h->x64, 0, n * sizeof(double), s));
+    NMG_CK(cudaMemsetAsync(h->cyc, 0, 4 * sizeof(int), s));
     launch_norm2(h->b64, n, h->partial, h->scal + S_BNORM, s);
     NMG_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     J.launches = g_launches - J.launches0;
@@ -689,26 +789,27 @@ static void job_advance(SolveJob& J) {
             job_fail(J, NMG_ERR_NOT_CONVERGED);
             job_enqueue_finish(J);
         } else {
-            J.j = 0;
             job_enqueue_iter(J);
         }
         break;
     }
     case SolveJob::P_ITER: {
-        ++J.its;
-        const int k = J.j + 1;
+        // the device counted the steps and decided whether the cycle stops
+        const int* cy = h->host_cyc;
+        const int k = cy[0] + 1;   // steps of this cycle
+        if (J.loop) J.launches += h->cgraph_nodes[J.o.precision] * (int64_t)(cy[1] - J.its);
+        J.its = cy[1];
         if (hs[S_STATUS] != 0.0) {
             fail(NMG_ERR_NONFINITE, "non-finite value in the Arnoldi process");
             job_fail(J, NMG_ERR_NONFINITE);
             job_enqueue_finish(J);
-        } else if (hs[S_EST] <= J.o.rtol || J.its >= J.o.maxit || hs[S_INVH] == 0.0 || k == J.o.restart) {
+        } else if (cy[2]) {
             const Geom& g = h->lev[h->L - 1].g;
             const int64_t n = g.nodes * g.nc;
             launch_solve_update(h->scal, k, J.o.restart, h->Z, n, h->x64, n, h->stream);
             ++J.cycles;
             job_enqueue_cycle(J);
         } else {
-            J.j = k;
             job_enqueue_iter(J);
         }
         break;
@@ -747,6 +848,7 @@ static void job_info(const SolveJob& J, nmg_solve_info* info) {
     info->status = J.st;
     info->launches = J.launches;
     info->engine = J.engine;
+    info->device_loop = J.used_loop ? 1 : 0;
 }
 
 static nmg_status solve_impl(Hierarchy* h, const double* b_user, double* x_user, const nmg_solve_opts& o,
@@ -785,18 +887,22 @@ nmg_status nmg_default_opts(nmg_solve_opts* o) {
     o->omega = 0.8;
     o->precision = NMG_PREC_FP32;
     o->weighting = NMG_WEIGHT_AVERAGE;
-    o->use_graph = 1;
+    o->use_graph = 2;
     o->engine = NMG_ENGINE_AUTO;
+    o->tail_patches = 0;
     return NMG_OK;
 }
 
 static void free_all(Hierarchy* h) {
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p) {
         if (h->vgraph[p]) cudaGraphExecDestroy(h->vgraph[p]);
+        if (h->cgraph[p]) cudaGraphExecDestroy(h->cgraph[p]);
+    }
     for (void* a : h->allocs) cudaFree(a);
     h->allocs.clear();
     if (h->host_scal) cudaFreeHost(h->host_scal);
     if (h->host_flags) cudaFreeHost(h->host_flags);
+    if (h->host_cyc) cudaFreeHost(h->host_cyc);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     if (h->desc.stream == nullptr && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -897,10 +1003,12 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if ((st = dalloc(h, (void**)&h->flags, FLAG_COUNT * sizeof(int))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->pbar, 2 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
     if ((st = dalloc(h, (void**)&h->counters, 4 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
+    if ((st = dalloc(h, (void**)&h->cyc, 4 * sizeof(int))) != NMG_OK) return cleanup(st);
     if (cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
     if (cudaMemset(h->flags, 0, FLAG_COUNT * sizeof(int)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
     if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess)
+        cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->host_cyc, 4 * sizeof(int)) != cudaSuccess)
         return cleanup(fail(NMG_ERR_OOM, "pinned host allocation failed"));
     *out = h;
     return NMG_OK;
@@ -1137,7 +1245,7 @@ nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
     std::string js = "{\"choice\": [";
     for (int p = 0; p < 3; ++p) {
         js += "{\"precision\": " + std::to_string(p) + ", \"engine\": " + std::to_string(h->engine_choice[p]) +
-              ", \"tail_patches\": " + std::to_string(h->tail_patches[p]) +
+              ", \"tail_patches\": " + std::to_string(h->auto_tail[p]) +
               ", \"fused\": " + std::to_string(h->fused[p]) + "}";
         if (p < 2) js += ", ";
     }
@@ -1150,7 +1258,9 @@ nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
         js += tmp;
         if (i + 1 < h->tuning.size()) js += ", ";
     }
-    js += "]}";
+    js += "], \"device_loop\": {\"mode\": " + std::to_string(h->loop_mode) + ", \"kernels_per_step\": [" +
+          std::to_string(h->cgraph_nodes[0]) + ", " + std::to_string(h->cgraph_nodes[1]) + ", " +
+          std::to_string(h->cgraph_nodes[2]) + "]}}";
     if (js.size() + 1 > len) return fail(NMG_ERR_INVALID, "buffer too small");
     std::memcpy(buf, js.c_str(), js.size() + 1);
     return NMG_OK;

@@ -319,6 +319,19 @@ __device__ __forceinline__ void mbar_init(uint32_t bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Asynchronous copy of one 4- or 8-byte element global -> shared (cp.async;
+// completion tracked per thread by commit / wait groups).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One TMA bulk copy of `bytes` (multiple of 16, 16-byte aligned ends) completing on bar.
 __device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");

@@ -1,8 +1,9 @@
 // FP64 kernels of the outer flexible GMRES (Section 4.3 item (I)): classical
-// Gram-Schmidt with re-orthogonalisation (two passes of one multi-dot and one
-// multi-axpy each), norms, the Givens update of the Hessenberg column and the
-// final x += Z y.  All reductions use a fixed grid and a fixed summation tree,
-// so results are bitwise reproducible run to run.
+// Gram-Schmidt with re-orthogonalisation (a multi-dot, a fused multi-axpy +
+// multi-dot, a multi-axpy + norm), the Givens update of the Hessenberg column,
+// the on-device step decision and the final x += Z y.  All reductions use a
+// fixed grid and a fixed summation tree, so results are bitwise reproducible
+// run to run.
 #include "nmg_internal.cuh"
 
 namespace nmg {
@@ -10,7 +11,6 @@ namespace nmg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = 8;     // Krylov vectors per pass of the multi-dot
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -22,31 +22,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
     __syncthreads();
     return r;   // valid in thread 0
-}
-
-// partial[k * kDotBlocks + blk] = sum over this block's indices of V_k . w
-__global__ void __launch_bounds__(kThreads)
-k_multidot_partial(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w,
-                   int64_t n, double* __restrict__ partial) {
-    NMG_PDL_ENTRY();
-    __shared__ double red[kThreads / 32];
-    for (int kc = 0; kc < nvec; kc += kChunk) {
-        double acc[kChunk];
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
-            const double wi = w[i];
-#pragma unroll
-            for (int q = 0; q < kChunk; ++q)
-                if (kc + q < nvec) acc[q] = fma(V[(int64_t)(kc + q) * ldv + i], wi, acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            if (kc + q >= nvec) break;
-            const double s = block_sum(acc[q], red);
-            if (threadIdx.x == 0) partial[(int64_t)(kc + q) * kDotBlocks + blockIdx.x] = s;
-        }
-    }
 }
 
 // out[k] (+)= sum_blk partial[k][blk], one warp per k, fixed order.
@@ -65,28 +40,6 @@ __global__ void k_finish_dots(const double* __restrict__ partial, int nvec, doub
     }
 }
 
-// w -= sum_k h_k V_k ; partial[blk] = sum over block of w_new^2
-__global__ void __launch_bounds__(kThreads)
-k_gs_update(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
-            double* __restrict__ w, int64_t n, double* __restrict__ partial, bool want_norm) {
-    NMG_PDL_ENTRY();
-    __shared__ double red[kThreads / 32];
-    __shared__ double hs[kMaxRestart + 1];
-    for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
-    __syncthreads();
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
-        double v = w[i];
-        for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
-        w[i] = v;
-        acc = fma(v, v, acc);
-    }
-    if (want_norm) {
-        const double s = block_sum(acc, red);
-        if (threadIdx.x == 0) partial[blockIdx.x] = s;
-    }
-}
-
 __global__ void __launch_bounds__(kThreads)
 k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ partial) {
     NMG_PDL_ENTRY();
@@ -98,50 +51,56 @@ k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ pa
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// Column j of the Hessenberg matrix from scal[S_HC + 0..j+1] (h_{0..j,j} and
-// ||w||): apply the earlier rotations, build rotation j, update g, write the
-// residual estimate |g_{j+1}| / ||b|| and 1 / h_{j+1,j}.
-__device__ void arnoldi_column(double* scal, int j, int m) {
-    double* H = scal + S_H + (int64_t)j * (m + 1);
-    const double* hc = scal + S_HC;
-    double* cs = scal + S_CS;
-    double* sn = scal + S_SN;
-    double* g = scal + S_G;
-    // two Gram-Schmidt passes: coefficients of pass 1 in hc, of pass 2 in scal[S_Y]
-    for (int i = 0; i <= j; ++i) H[i] = hc[i] + scal[S_Y + i];
-    H[j + 1] = hc[j + 1];
-    const double hnext = hc[j + 1];
-    for (int i = 0; i < j; ++i) {
-        const double a = H[i], b = H[i + 1];
-        H[i] = cs[i] * a + sn[i] * b;
-        H[i + 1] = -sn[i] * a + cs[i] * b;
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes
+// (coefficients scal[S_HC + i] + scal[S_Y + i], i <= j) and h_{j+1,j} = hnext:
+// apply the earlier rotations, build rotation j, update g, write the residual
+// estimate |g_{j+1}| / ||b|| and 1 / h_{j+1,j}.  Called by a whole block: the
+// inputs are first staged in shared memory by all threads (one memory latency
+// instead of one per rotation), then thread 0 runs the serial recurrence.
+__device__ void arnoldi_column(double* scal, int j, int m, double hnext) {
+    __shared__ double sH[kMaxRestart + 2], scs[kMaxRestart], ssn[kMaxRestart];
+    __shared__ double sg, sbn;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) sH[i] = scal[S_HC + i] + scal[S_Y + i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        scs[i] = scal[S_CS + i];
+        ssn[i] = scal[S_SN + i];
     }
-    const double a = H[j], b = H[j + 1];
+    if (threadIdx.x == 0) {
+        sH[j + 1] = hnext;
+        sg = scal[S_G + j];
+        sbn = scal[S_BNORM];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double* H = scal + S_H + (int64_t)j * (m + 1);
+    for (int i = 0; i < j; ++i) {
+        const double a = sH[i], b = sH[i + 1];
+        sH[i] = scs[i] * a + ssn[i] * b;
+        sH[i + 1] = -ssn[i] * a + scs[i] * b;
+    }
+    const double a = sH[j], b = sH[j + 1];
     double c, s;
     if (b == 0.0) { c = a >= 0.0 ? 1.0 : -1.0; s = 0.0; }
     else { const double r = hypot(a, b); c = a / r; s = b / r; }
-    cs[j] = c;
-    sn[j] = s;
+    for (int i = 0; i < j; ++i) H[i] = sH[i];
     H[j] = c * a + s * b;
     H[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    const double est = fabs(g[j + 1]) / scal[S_BNORM];
+    scal[S_CS + j] = c;
+    scal[S_SN + j] = s;
+    scal[S_G + j + 1] = -s * sg;
+    scal[S_G + j] = c * sg;
+    const double est = fabs(-s * sg) / sbn;
     scal[S_EST] = est;
     scal[S_INVH] = hnext != 0.0 ? 1.0 / hnext : 0.0;
     if (!isfinite(est) || !isfinite(hnext)) scal[S_STATUS] = (double)NMG_ERR_NONFINITE;
     scal[S_ITER] += 1.0;
 }
 
-__global__ void k_arnoldi_finish(double* scal, int j, int m) {
+__global__ void k_start_cycle(double* scal, int m, int* cyc) {
     NMG_PDL_ENTRY();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    arnoldi_column(scal, j, m);
-}
-
-__global__ void k_start_cycle(double* scal, int m) {
-    NMG_PDL_ENTRY();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    cyc[0] = 0;
+    cyc[2] = 0;
     for (int i = 0; i <= m; ++i) scal[S_G + i] = 0.0;
     const double beta = scal[S_BETA];
     scal[S_G] = beta;
@@ -149,24 +108,23 @@ __global__ void k_start_cycle(double* scal, int m) {
     if (!isfinite(beta)) scal[S_STATUS] = (double)NMG_ERR_NONFINITE;
 }
 
-__global__ void k_scale(const double* __restrict__ x, const double* __restrict__ sp, double* __restrict__ y, int64_t n) {
+// y = H[:k,:k]^{-1} g[:k] by back substitution: the triangle and g are
+// staged in shared memory by the block, then thread 0 substitutes.
+__global__ void __launch_bounds__(kThreads) k_backsolve(double* scal, int k, int m) {
     NMG_PDL_ENTRY();
-    const double a = *sp;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a * x[i];
-}
-
-// y = H[:k,:k]^{-1} g[:k] by back substitution (single thread).
-__global__ void k_backsolve(double* scal, int k, int m) {
-    NMG_PDL_ENTRY();
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sH[kMaxRestart * (kMaxRestart + 1)];
+    __shared__ double sg[kMaxRestart], ys[kMaxRestart];
     const double* H = scal + S_H;
+    for (int i = threadIdx.x; i < k * (m + 1); i += blockDim.x) sH[i] = H[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sg[i] = scal[S_G + i];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double* y = scal + S_Y;
-    const double* g = scal + S_G;
     for (int i = k - 1; i >= 0; --i) {
-        double v = g[i];
-        for (int c = i + 1; c < k; ++c) v -= H[(int64_t)c * (m + 1) + i] * y[c];
-        y[i] = v / H[(int64_t)i * (m + 1) + i];
+        double v = sg[i];
+        for (int c = i + 1; c < k; ++c) v -= sH[c * (m + 1) + i] * ys[c];
+        ys[i] = v / sH[i * (m + 1) + i];
+        y[i] = ys[i];
     }
 }
 
@@ -184,12 +142,6 @@ k_update_x(const double* __restrict__ scal, int k, const double* __restrict__ Z,
     }
 }
 
-__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, int64_t n) {
-    NMG_PDL_ENTRY();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
-}
-
 inline unsigned grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     if (b > 4096) b = 4096;
@@ -198,10 +150,19 @@ inline unsigned grid_for(int64_t n) {
 
 
 // Sum over the kDotBlocks partials of row k in the fixed order of
-// k_finish_dots (lane-strided, then a shuffle tree); valid in lane 0.
+// k_finish_dots (lane-strided, then a shuffle tree); valid in lane 0.  The
+// loads of a lane are issued together (one memory latency per row).
 __device__ __forceinline__ double finish_row(const double* __restrict__ partial, int k, int lane) {
+    constexpr int R = (kDotBlocks + 31) / 32;
+    double v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int b = lane + 32 * r;
+        v[r] = b < kDotBlocks ? partial[(int64_t)k * kDotBlocks + b] : 0.0;
+    }
     double s = 0.0;
-    for (int b = lane; b < kDotBlocks; b += 32) s += partial[(int64_t)k * kDotBlocks + b];
+#pragma unroll
+    for (int r = 0; r < R; ++r) s += v[r];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     return s;
 }
@@ -222,51 +183,154 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
     return s_last != 0;
 }
 
-// out[k] = V_k . w for k < nvec, in one launch.
-__global__ void __launch_bounds__(kThreads)
-k_multidot_fused(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ w, int64_t n,
-                 double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
-    NMG_PDL_ENTRY();
-    __shared__ double red[kThreads / 32];
-    for (int kc = 0; kc < nvec; kc += kChunk) {
-        double acc[kChunk];
+// Multi-dot machinery.  FP64 arithmetic is the scarce resource of these
+// kernels (the FP64 pipe of an SM retires about one FMA per clock), so the
+// reductions are built to spend few FP64 additions: a thread accumulates up to
+// 32 dot products over ~n / 19k elements, a warp reduces its 32 values by a
+// transposing butterfly (31 additions per lane instead of 5 per value), the
+// block adds its warps, and the last block sums the block partials in a fixed
+// order.  Results are bitwise reproducible run to run.
+constexpr int kMdThreads = 64;
+constexpr int kMdWarps = kMdThreads / 32;
+constexpr int kMdChunk = 32;   // vectors per pass over w
+
+// After the call lane l holds the warp's total of a[l].
+__device__ __forceinline__ double butterfly32(double (&a)[kMdChunk], int lane) {
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
-            const double wi = w[i];
+    for (int c = kMdChunk / 2; c >= 1; c >>= 1) {
+        const bool upper = (lane & c) != 0;
 #pragma unroll
-            for (int q = 0; q < kChunk; ++q)
-                if (kc + q < nvec) acc[q] = fma(V[(int64_t)(kc + q) * ldv + i], wi, acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            if (kc + q >= nvec) break;
-            const double s = block_sum(acc[q], red);
-            if (threadIdx.x == 0) partial[(int64_t)(kc + q) * kDotBlocks + blockIdx.x] = s;
+        for (int q = 0; q < c; ++q) {
+            const double keep = upper ? a[c + q] : a[q];
+            const double send = upper ? a[q] : a[c + q];
+            a[q] = keep + __shfl_xor_sync(0xffffffffu, send, c);
         }
     }
-    if (!last_block(counter)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < nvec; k += kThreads / 32) {
-        const double s = finish_row(partial, k, lane);
-        if (lane == 0) out[k] = s;
+    return a[0];
+}
+
+// Block total of the chunk's 32 values -> partial[(chunk * grid + block) * 32 + l].
+__device__ __forceinline__ void block_partials(double (&acc)[kMdChunk], double* __restrict__ partial, int chunk,
+                                               int lane, int warp) {
+    __shared__ double red[kMdWarps][kMdChunk];
+    red[warp][lane] = butterfly32(acc, lane);
+    __syncthreads();
+    if (warp == 0) {
+        double t = red[0][lane];
+#pragma unroll
+        for (int ww = 1; ww < kMdWarps; ++ww) t += red[ww][lane];
+        partial[((int64_t)chunk * gridDim.x + blockIdx.x) * kMdChunk + lane] = t;
+    }
+    __syncthreads();
+}
+
+// In the last block: out[k] = sum over the blocks of the partials of value k
+// (warp w sums the blocks w, w + kMdWarps, ..., then the warps are added).
+__device__ void finish_chunks(const double* __restrict__ partial, int nvec, double* __restrict__ out, int lane,
+                              int warp) {
+    __shared__ double fs[kMdWarps][kMdChunk];
+    const int G = gridDim.x;
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
+        const double* p = partial + (int64_t)chunk * G * kMdChunk + lane;
+        double s = 0.0;
+        int b = warp;
+        for (; b + 7 * kMdWarps < G; b += 8 * kMdWarps) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(b + u * kMdWarps) * kMdChunk];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; b < G; b += kMdWarps) s += p[(int64_t)b * kMdChunk];
+        fs[warp][lane] = s;
+        __syncthreads();
+        if (warp == 0 && c0 + lane < nvec) {
+            double t = fs[0][lane];
+#pragma unroll
+            for (int ww = 1; ww < kMdWarps; ++ww) t += fs[ww][lane];
+            out[c0 + lane] = t;
+        }
+        __syncthreads();
     }
 }
 
+// out[k] = V_k . w for the nvec = cyc[0] + 1 vectors of the current Arnoldi
+// step (first Gram-Schmidt pass), in one launch.
+__global__ void __launch_bounds__(kMdThreads)
+k_multidot_fused(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ w,
+                 int64_t n, double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
+    NMG_PDL_ENTRY();
+    const int nvec = cyc[0] + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t T = (int64_t)gridDim.x * kMdThreads;
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
+        const int nv = min(kMdChunk, nvec - c0);
+        double acc[kMdChunk];
+#pragma unroll
+        for (int k = 0; k < kMdChunk; ++k) acc[k] = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
+            const double wi = w[i];
+#pragma unroll
+            for (int k = 0; k < kMdChunk; ++k)
+                if (k < nv) acc[k] = fma(V[(int64_t)(c0 + k) * ldv + i], wi, acc[k]);
+        }
+        block_partials(acc, partial, chunk, lane, warp);
+    }
+    if (!last_block(counter)) return;
+    finish_chunks(partial, nvec, out, lane, warp);
+}
+
+// Second Gram-Schmidt pass fused with the first update: w <- w - sum_k h_k V_k
+// (h = the first pass's coefficients) and out[k] = V_k . w_new, reading V
+// once for both.
+__global__ void __launch_bounds__(kMdThreads)
+k_gs_update_dot(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ h,
+                double* __restrict__ w, int64_t n, double* __restrict__ partial, double* __restrict__ out,
+                unsigned* counter) {
+    NMG_PDL_ENTRY();
+    __shared__ double hs[kMaxRestart + 1];
+    const int nvec = cyc[0] + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < nvec; k += kMdThreads) hs[k] = h[k];
+    __syncthreads();
+    const int64_t T = (int64_t)gridDim.x * kMdThreads;
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
+        const int nv = min(kMdChunk, nvec - c0);
+        double acc[kMdChunk];
+#pragma unroll
+        for (int k = 0; k < kMdChunk; ++k) acc[k] = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
+            double v = w[i];
+            if (chunk == 0) {
+#pragma unroll 8
+                for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
+                w[i] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < kMdChunk; ++k)
+                if (k < nv) acc[k] = fma(V[(int64_t)(c0 + k) * ldv + i], v, acc[k]);
+        }
+        block_partials(acc, partial, chunk, lane, warp);
+    }
+    if (!last_block(counter)) return;
+    finish_chunks(partial, nvec, out, lane, warp);
+}
+
 // Second Gram-Schmidt pass w -= sum h_k V_k, ||w|| into scal[S_HC + j + 1], then
-// the Givens update of Hessenberg column j, in one launch.
+// the Givens update of Hessenberg column j = cyc[0], in one launch.
 __global__ void __launch_bounds__(kThreads)
-k_gs_norm_arnoldi(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
-                  double* __restrict__ w, int64_t n, double* __restrict__ partial, double* scal, int j, int m,
-                  unsigned* counter) {
+k_gs_norm_arnoldi(const double* __restrict__ V, int64_t ldv, const double* __restrict__ h, double* __restrict__ w,
+                  int64_t n, double* __restrict__ partial, double* scal, const int* cyc, int m, unsigned* counter) {
     NMG_PDL_ENTRY();
     __shared__ double red[kThreads / 32];
     __shared__ double hs[kMaxRestart + 1];
+    const int j = cyc[0], nvec = j + 1;
     for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
     __syncthreads();
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
         double v = w[i];
+#pragma unroll 8
         for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
         w[i] = v;
         acc = fma(v, v, acc);
@@ -274,26 +338,50 @@ k_gs_norm_arnoldi(const double* __restrict__ V, int64_t ldv, int nvec, const dou
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
     if (!last_block(counter)) return;
+    __shared__ double s_hnext;
     if (threadIdx.x < 32) {
         const double t = finish_row(partial, 0, threadIdx.x);
         if (threadIdx.x == 0) {
-            scal[S_HC + j + 1] = sqrt(t);
-            arnoldi_column(scal, j, m);
+            s_hnext = sqrt(t);
+            scal[S_HC + j + 1] = s_hnext;
         }
     }
+    __syncthreads();
+    arnoldi_column(scal, j, m, s_hnext);
 }
 
-// y = x * scal[S_INVH] (the next Krylov vector) and, when y32 is given, its
-// FP32 copy (the right-hand side of the next reduced-precision V-cycle).
-__global__ void k_scale_convert(const double* __restrict__ x, const double* __restrict__ sp, double* __restrict__ y,
-                                float* __restrict__ y32, int64_t n) {
+// v = x * scal[S_INVH] into the Krylov basis (column cyc[0] + 1 when next,
+// else column 0) and its copy in the V-cycle's arithmetic type TV (the
+// right-hand side of the next V-cycle).
+template <typename TV>
+__global__ void k_scale_convert(const double* __restrict__ x, const double* __restrict__ sp, double* __restrict__ V,
+                                int64_t ldv, const int* __restrict__ cyc, bool next, TV* __restrict__ vin, int64_t n) {
     NMG_PDL_ENTRY();
     const double a = *sp;
+    double* y = V + (next ? (int64_t)(cyc[0] + 1) * ldv : 0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = a * x[i];
         y[i] = v;
-        if (y32) y32[i] = (float)v;
+        vin[i] = (TV)v;
     }
+}
+
+// End of one Arnoldi step: counts the iteration and decides on the device
+// whether the cycle goes on (estimate above rtol, iterations below maxit, no
+// breakdown, no non-finite value, basis not full); cyc[2] = 1 once it stops.
+// Inside a graph loop the decision also sets the loop's condition.
+__global__ void k_decide(const double* __restrict__ scal, int* cyc, double rtol, int maxit, int m,
+                         cudaGraphConditionalHandle loop, bool in_loop) {
+    NMG_PDL_ENTRY();
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = cyc[0];
+    const int its = cyc[1] + 1;
+    cyc[1] = its;
+    const bool stop = scal[S_STATUS] != 0.0 || scal[S_EST] <= rtol || its >= maxit || scal[S_INVH] == 0.0 ||
+                      j + 1 >= m;
+    cyc[2] = stop ? 1 : 0;
+    if (!stop) cyc[0] = j + 1;
+    if (in_loop) cudaGraphSetConditional(loop, stop ? 0u : 1u);
 }
 
 }  // namespace
@@ -304,63 +392,56 @@ void launch_norm2(const double* x, int64_t n, double* partial, double* out, cuda
     pdl_launch(k_finish_dots, dim3(1), dim3(32), 0, s, partial, 1, out, false, true);
 }
 
-void launch_multidot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
-                     double* out, bool accumulate, cudaStream_t s) {
-    g_launches += 2;
-    pdl_launch(k_multidot_partial, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, w, n, partial);
-    pdl_launch(k_finish_dots, dim3((nvec + 7) / 8), dim3(256), 0, s, partial, nvec, out, accumulate, false);
-}
-
-void launch_gs_update(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
-                      double* partial, double* nrm2, bool want_norm, cudaStream_t s) {
-    g_launches += want_norm ? 2 : 1;
-    pdl_launch(k_gs_update, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, h, w, n, partial, want_norm);
-    if (want_norm) pdl_launch(k_finish_dots, dim3(1), dim3(32), 0, s, partial, 1, nrm2, false, true);
-}
-
-void launch_arnoldi_finish(double* scal, int j, int m, cudaStream_t s) { pdl_launch(k_arnoldi_finish, dim3(1), dim3(32), 0, s, scal, j, m); }
-
-void launch_scale(const double* x, const double* scal_ptr, bool invert, double* y, int64_t n, cudaStream_t s) {
+void launch_start_cycle(double* scal, int m, int* cyc, cudaStream_t s) {
     g_launches += 1;
-    (void)invert;
-    pdl_launch(k_scale, dim3(grid_for(n)), dim3(256), 0, s, x, scal_ptr, y, n);
+    pdl_launch(k_start_cycle, dim3(1), dim3(32), 0, s, scal, m, cyc);
 }
-
-void launch_start_cycle(double* scal, int m, cudaStream_t s) { pdl_launch(k_start_cycle, dim3(1), dim3(32), 0, s, scal, m); }
 
 void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x, int64_t n,
                          cudaStream_t s) {
     g_launches += 2;
-    pdl_launch(k_backsolve, dim3(1), dim3(32), 0, s, scal, k, m);
+    pdl_launch(k_backsolve, dim3(1), dim3(kThreads), 0, s, scal, k, m);
     pdl_launch(k_update_x, dim3(grid_for(n)), dim3(kThreads), 0, s, scal, k, Z, ldz, x, n);
-}
-
-void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s) {
-    g_launches += 1;
-    pdl_launch(k_axpby, dim3(grid_for(n)), dim3(256), 0, s, a, x, b, y, n);
 }
 
 }  // namespace nmg
 
 namespace nmg {
 
-void launch_multidot_fused(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
+void launch_multidot_fused(const double* V, int64_t ldv, const int* cyc, const double* w, int64_t n, double* partial,
                            double* out, unsigned* counter, cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_multidot_fused, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, w, n, partial, out, counter);
+    pdl_launch(k_multidot_fused, dim3(kDotBlocks), dim3(kMdThreads), 0, s, V, ldv, cyc, w, n, partial, out, counter);
 }
 
-void launch_gs_norm_arnoldi(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
-                            double* partial, double* scal, int j, int m, unsigned* counter, cudaStream_t s) {
+void launch_gs_update_dot(const double* V, int64_t ldv, const int* cyc, const double* h, double* w, int64_t n,
+                          double* partial, double* out, unsigned* counter, cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_gs_norm_arnoldi, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, nvec, h, w, n, partial, scal, j,
-               m, counter);
+    pdl_launch(k_gs_update_dot, dim3(kDotBlocks), dim3(kMdThreads), 0, s, V, ldv, cyc, h, w, n, partial, out, counter);
 }
 
-void launch_scale_convert(const double* x, const double* scal_ptr, double* y, float* y32, int64_t n,
-                          cudaStream_t s) {
+void launch_gs_norm_arnoldi(const double* V, int64_t ldv, const double* h, double* w, int64_t n, double* partial,
+                            double* scal, const int* cyc, int m, unsigned* counter, cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_scale_convert, dim3(grid_for(n)), dim3(256), 0, s, x, scal_ptr, y, y32, n);
+    pdl_launch(k_gs_norm_arnoldi, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, h, w, n, partial, scal, cyc, m,
+               counter);
+}
+
+template <typename TV>
+void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,
+                          TV* vin, int64_t n, cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_scale_convert<TV>, dim3(grid_for(n)), dim3(256), 0, s, x, scal_ptr, V, ldv, cyc, next, vin, n);
+}
+template void launch_scale_convert<float>(const double*, const double*, double*, int64_t, const int*, bool, float*,
+                                          int64_t, cudaStream_t);
+template void launch_scale_convert<double>(const double*, const double*, double*, int64_t, const int*, bool, double*,
+                                           int64_t, cudaStream_t);
+
+void launch_decide(const double* scal, int* cyc, double rtol, int maxit, int m, cudaGraphConditionalHandle loop,
+                   bool in_loop, cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_decide, dim3(1), dim3(32), 0, s, scal, cyc, rtol, maxit, m, loop, in_loop);
 }
 
 }  // namespace nmg

@@ -15,6 +15,7 @@ namespace nmg {
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxRestart = 64;
+constexpr int kMaxDevices = 64;       // per-device caches of launch shapes
 constexpr int kDotBlocks = 296;        // fixed grid of the deterministic reductions (2 x 148)
 
 // ---------------------------------------------------------------------------
@@ -75,12 +76,24 @@ struct Hierarchy {
     double* w64 = nullptr;        // Arnoldi vector
     double* V = nullptr;          // (m + 1) Krylov vectors
     double* Z = nullptr;          // m preconditioned vectors
-    double* partial = nullptr;    // kMaxRestart + 2 rows of kDotBlocks partial sums
+    double* partial = nullptr;    // block partial sums of the reductions ((kMaxRestart + 2) * kDotBlocks)
     double* scal = nullptr;       // device scalars (see krylov kernels)
     double* host_scal = nullptr;  // pinned mirror of a few scalars
     int* host_flags = nullptr;    // pinned mirror of the flags and the wait-timeout flag
     int* flags = nullptr;         // device error flags
+    int* cyc = nullptr;           // device state of the restart cycle: step j, iterations, stopped
+    int* host_cyc = nullptr;      // pinned mirror of cyc
     int m_alloc = 0;
+    int krylov_gen = 0;           // bumped when V / Z are reallocated
+    // restart cycles as one graph with an on-device loop, per precision
+    struct LoopKey {
+        int nu1, nu2, weighting, engine, tail, restart, maxit, gen;
+        double omega, rtol;
+    };
+    cudaGraphExec_t cgraph[3] = {nullptr, nullptr, nullptr};
+    LoopKey cgraph_key[3] = {};
+    int64_t cgraph_nodes[3] = {0, 0, 0};   // kernels per loop step
+    int loop_mode = 0;                     // 0 untried, 1 with PDL edges, 2 without, -1 unavailable
     size_t bytes = 0;
     // CUDA graphs of the V-cycle, per precision (rebuilt when options change)
     cudaGraphExec_t vgraph[3] = {nullptr, nullptr, nullptr};
@@ -99,7 +112,8 @@ struct Hierarchy {
     unsigned* counters = nullptr;        // last-block tickets of the fused reductions
     int engine_choice[3] = {0, 0, 0};
     int fused[3] = {0, 0, 0};            // per-step engine: fused update/prolongation + residual kernels
-    int tail_patches[3] = {0, 0, 0};     // levels with at most this many patches run in the one-CTA tail
+    int tail_patches[3] = {0, 0, 0};     // levels with at most this many patches run in the cluster tail
+    int auto_tail[3] = {0, 0, 0};        // the autotuner's pick of tail_patches
                                          // (0: none; the autotuner may pick a threshold)
     int engine_key[3][3] = {};
     double engine_us[3][2] = {};
@@ -116,7 +130,7 @@ enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_AB
 struct Hierarchy;
 cudaError_t launch_vcycle_persistent(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting,
                                      unsigned* bar, int* abort, int small_patches);
-// Levels 0..top of a V-cycle on one CTA (persistent.cu).
+// Levels 0..top of a V-cycle as one thread-block-cluster launch (cluster.cu).
 void launch_vcycle_tail(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
                         const void* b_top, void* x_top);
 
@@ -180,26 +194,27 @@ enum Scal {
     S_COUNT = S_HC + kMaxRestart + 2
 };
 void launch_norm2(const double* x, int64_t n, double* partial, double* out, cudaStream_t s);
-void launch_multidot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
-                     double* partial, double* out, bool accumulate, cudaStream_t s);
-void launch_gs_update(const double* V, int64_t ldv, int nvec, const double* h, double* w,
-                      int64_t n, double* partial, double* nrm2, bool want_norm, cudaStream_t s);
-void launch_arnoldi_finish(double* scal, int j, int m, cudaStream_t s);
-void launch_scale(const double* x, const double* scal_ptr, bool invert, double* y, int64_t n,
-                  cudaStream_t s);
-void launch_start_cycle(double* scal, int m, cudaStream_t s);
+// Kernels of one FGMRES step.  The step index j of the current restart cycle
+// lives on the device (cyc[0]; cyc[1] = iterations so far, cyc[2] = 1 once the
+// cycle has stopped), so the same launches serve every step and can be
+// replayed by a graph loop.
+void launch_start_cycle(double* scal, int m, int* cyc, cudaStream_t s);
 void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x,
                          int64_t n, cudaStream_t s);
-void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
-// fused forms used by the solve (same summation orders as the separate kernels)
-void launch_multidot_fused(const double* V, int64_t ldv, int nvec, const double* w, int64_t n, double* partial,
+void launch_multidot_fused(const double* V, int64_t ldv, const int* cyc, const double* w, int64_t n, double* partial,
                            double* out, unsigned* counter, cudaStream_t s);
-void launch_gs_norm_arnoldi(const double* V, int64_t ldv, int nvec, const double* h, double* w, int64_t n,
-                            double* partial, double* scal, int j, int m, unsigned* counter, cudaStream_t s);
-void launch_scale_convert(const double* x, const double* scal_ptr, double* y, float* y32, int64_t n,
-                          cudaStream_t s);
+void launch_gs_update_dot(const double* V, int64_t ldv, const int* cyc, const double* h, double* w, int64_t n,
+                          double* partial, double* out, unsigned* counter, cudaStream_t s);
+void launch_gs_norm_arnoldi(const double* V, int64_t ldv, const double* h, double* w, int64_t n, double* partial,
+                            double* scal, const int* cyc, int m, unsigned* counter, cudaStream_t s);
+template <typename TV>
+void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,
+                          TV* vin, int64_t n, cudaStream_t s);
+void launch_decide(const double* scal, int* cyc, double rtol, int maxit, int m, cudaGraphConditionalHandle loop,
+                   bool in_loop, cudaStream_t s);
 template <typename TX>
-void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* z64, double* w, cudaStream_t s);
+void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* Z, int64_t ldz, const int* cyc, double* w,
+                        cudaStream_t s);
 
 }  // namespace nmg
 
@@ -207,6 +222,9 @@ namespace nmg {
 // Kernels enqueued by the calling thread (launchers add to it; a graph replay
 // adds the number of kernel nodes it holds).
 extern thread_local int64_t g_launches;
+// Set while a graph body is captured whose kernels must not carry programmatic
+// (PDL) launch edges.
+extern thread_local bool g_no_pdl;
 
 // Programmatic dependent launch: every solve-phase kernel is launched with
 // programmatic stream serialisation, so its launch overlaps the drain of the
@@ -230,7 +248,7 @@ inline void pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_no_pdl ? 0 : 1;
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 

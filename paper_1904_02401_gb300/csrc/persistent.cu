@@ -288,17 +288,6 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vcycle_persistent(const __grid
     vc.run();
 }
 
-// Tail of a V-cycle on one CTA: levels 0..top of the hierarchy, every phase
-// separated by __syncthreads only (no grid barrier, no cooperative launch).
-template <typename T, typename TS, int DIM>
-__global__ void __launch_bounds__(kPThreads, 1) k_vcycle_tail(const __grid_constant__ PArgs a) {
-    NMG_PDL_ENTRY();
-    constexpr int NP = VCycle<T, TS, DIM>::NP;
-    __shared__ T sd[kPWarps][NP];
-    VCycle<T, TS, DIM> vc(a, sd, nullptr, nullptr, 0u, 0u);
-    vc.run();
-}
-
 int sm_count_persistent() {
     static int n = 0;
     if (!n) {
@@ -332,56 +321,7 @@ cudaError_t launch_impl(const PArgs& a, size_t smem, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-template <typename T, typename TS, int DIM>
-void launch_tail_impl(const PArgs& a, cudaStream_t s) {
-    g_launches += 1;
-    pdl_launch(k_vcycle_tail<T, TS, DIM>, dim3(1), dim3(kPThreads), 0, s, a);
-}
-
 }  // namespace
-
-// Host entry: the V-cycle restricted to levels 0..top on one CTA.  The b of
-// level top is its right-hand side (b_top / x_top override the level's own
-// buffers when not null), x of level top receives the result.
-void launch_vcycle_tail(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
-                        const void* b_top, void* x_top) {
-    PArgs a{};
-    a.L = top + 1;
-    a.nu1 = nu1;
-    a.nu2 = nu2;
-    a.omega = omega;
-    a.average = weighting == NMG_WEIGHT_AVERAGE;
-    a.cinv = h->coarse_inv;
-    a.n0 = h->n0;
-    a.coarse_small = 1;
-    a.bar = h->pbar;
-    a.abort = h->flags + FLAG_ABORT;
-    for (int l = 0; l <= top; ++l) {
-        const Level& Lv = h->lev[l];
-        const PrecData& P = Lv.p[prec];
-        PLevel& q = a.lev[l];
-        q.g = Lv.g;
-        q.A = P.A;
-        q.inv = P.inv;
-        q.stride = P.inv_stride;
-        q.b = (l == top && b_top) ? const_cast<void*>(b_top) : P.b;
-        q.x = (l == top && x_top) ? x_top : P.x;
-        q.r = P.r;
-        q.corr = P.corr;
-        q.mask = Lv.mask;
-        q.small = 1;
-        q.staged = 0;
-    }
-    if (h->dim == 2) {
-        if (prec == NMG_PREC_FP64) launch_tail_impl<double, double, 2>(a, h->stream);
-        else if (prec == NMG_PREC_FP32) launch_tail_impl<float, float, 2>(a, h->stream);
-        else launch_tail_impl<float, __nv_bfloat16, 2>(a, h->stream);
-    } else {
-        if (prec == NMG_PREC_FP64) launch_tail_impl<double, double, 3>(a, h->stream);
-        else if (prec == NMG_PREC_FP32) launch_tail_impl<float, float, 3>(a, h->stream);
-        else launch_tail_impl<float, __nv_bfloat16, 3>(a, h->stream);
-    }
-}
 
 // Host entry: fills the launch arguments from the hierarchy and launches one
 // persistent V-cycle on the finest level's b/x buffers of precision prec.

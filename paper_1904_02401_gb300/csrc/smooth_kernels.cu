@@ -4,6 +4,8 @@
 // memory-bound; the data layouts are chosen so that warps read contiguous,
 // coalesced segments of the matrix and of the patch inverses.  All kernels are
 // launched with programmatic dependent launch (see nmg_internal.cuh).
+#include <algorithm>
+
 #include "elem.cuh"
 
 namespace nmg {
@@ -14,9 +16,9 @@ namespace {
 
 using namespace elem;
 
-constexpr int kPPC = 16;           // patches per CTA of the staged 2d apply
-constexpr int kStagedWarps = 4;
 constexpr int kWaitSpins = 1 << 22;
+constexpr int kRingThreads = 128;   // 4 warps: 4 x 27 rows of patch inverse per chunk
+constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CTA
 
 // y = A x  or  y = b - A x, one thread per node.  A in stencil layout.
 template <typename T, int DIM>
@@ -29,16 +31,17 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
 }
 
 // w = A z in FP64 with z read from the V-cycle output xf (stored as TX) and
-// written, converted, to z64 (the FGMRES basis vector Z_j): the outer product
-// of one FGMRES iteration without a separate conversion pass.
+// written, converted, to Z_j (the FGMRES basis vector of step j = cyc[0]):
+// the outer product of one FGMRES iteration without a separate conversion pass.
 template <typename TX, int DIM>
 __global__ void __launch_bounds__(256)
-k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ z64,
-              double* __restrict__ w) {
+k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ Z, int64_t ldz,
+              const int* __restrict__ cyc, double* __restrict__ w) {
     NMG_PDL_ENTRY();
     constexpr int NC = DIM + 1;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= g.nodes) return;
+    double* z64 = Z + (int64_t)cyc[0] * ldz;
 #pragma unroll
     for (int c = 0; c < NC; ++c) z64[i * NC + c] = (double)xf[i * NC + c];
     spmv_node<double, DIM, TX>(g, A, xf, nullptr, w, false, i);
@@ -64,43 +67,95 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
     apply_patch<T, TS, DIM, true>(inv + p * stride, sd[w], corr + p * NP, lane);
 }
 
-// 2d variant: the inverses of kPPC consecutive patches (contiguous in memory)
-// are staged into shared memory by one TMA bulk copy completing on an
-// mbarrier, so a CTA keeps kPPC * 2.9 KB (FP32) in flight instead of the few
-// hundred bytes a warp of per-lane loads keeps.  Each warp then applies its
-// patches from shared memory (same summation order as above).
-template <typename T, typename TS>
-__global__ void __launch_bounds__(kStagedWarps * 32)
-k_vanka_apply_staged2d(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
-                       T* __restrict__ corr) {
-    NMG_PDL_ENTRY();
-    constexpr int NP = 27;
+// Streaming apply for FP32 / BF16 inverses (2d and 3d): a persistent grid of
+// a few CTAs per SM walks the chunks c = blockIdx.x + k * gridDim.x; a chunk
+// is 4 patches in 2d (one warp per patch) or 1 patch in 3d (4 warps of 27
+// rows each), i.e. 4 x 27 rows in both.  Each CTA keeps STAGES chunk copies
+// of inverses (TMA bulk copies completing on one mbarrier per stage) and the
+// defect gathers of kGatherDepth chunks (cp.async) in flight, so neither the
+// DRAM queue nor the gather latency depends on how many warps are resident,
+// and there is no tail wave.  Row i of a patch is summed over the columns j in
+// ascending order with one fma per term, as in apply_patch, so the
+// corrections equal those of the other apply kernels bit for bit.
+template <typename T, typename TS, int DIM, int STAGES>
+__global__ void __launch_bounds__(kRingThreads)
+k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
+                   T* __restrict__ corr) {
+    constexpr int NC = DIM + 1;
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
+    constexpr int RW = NP / 27;                    // warps per patch
+    constexpr int CP = (kRingThreads / 32) / RW;   // patches per chunk
+    constexpr int GD = kGatherDepth;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ T sd[kPPC][NP];
-    TS* sinv = reinterpret_cast<TS*>(smem_raw);
-    const int tid = threadIdx.x;
-    const int w = tid >> 5, lane = tid & 31;
-    const int64_t p0 = (int64_t)blockIdx.x * kPPC;
-    const int count = (int)min((int64_t)kPPC, g.patches - p0);
-    const uint32_t bytes = (uint32_t)(count * stride * (int64_t)sizeof(TS));   // multiple of 16
-    const uint32_t bar = smem_addr(&mbar);
-    if (tid == 0) mbar_init(bar);
+    __shared__ __align__(8) uint64_t mbar[STAGES];
+    __shared__ T sd[GD + 1][CP][NP];
+    TS* ring = reinterpret_cast<TS*>(smem_raw);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int q = w / RW, row = (w % RW) * 27 + lane;
+    const int64_t G = gridDim.x;
+    const int64_t nchunks = (g.patches + CP - 1) / CP;
+    const int64_t mine = (nchunks - blockIdx.x + G - 1) / G;   // the grid is at most nchunks
+    const int64_t stage_elems = (int64_t)CP * stride;
+    auto issue = [&](int64_t k) {
+        const int64_t c = blockIdx.x + k * G;
+        const int cnt = (int)min((int64_t)CP, g.patches - c * CP);
+        bulk_copy(ring + (k % STAGES) * stage_elems, inv + c * CP * stride,
+                  (uint32_t)(cnt * stride * (int64_t)sizeof(TS)), smem_addr(&mbar[k % STAGES]));
+    };
+    // this thread's defect entry of chunk k -> sd[k % (GD + 1)], one commit group per chunk
+    auto gather = [&](int64_t k) {
+        const int64_t p = (blockIdx.x + k * G) * CP + q;
+        if (k < mine && lane < 27 && p < g.patches) {
+            int px, py, pz;
+            patch_xyz(g, p, px, py, pz);
+            const int an = row / NC, c = row - an * NC;
+            cp_async_elem(&sd[k % (GD + 1)][q][row], d + patch_node(g, px, py, pz, an) * NC + c);
+        }
+        cp_async_commit();
+    };
+    if (tid == 0)
+        for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(&mbar[st]));
     __syncthreads();
-    if (tid == 0) bulk_copy(sinv, inv + p0 * stride, bytes, bar);
-    // gather the defects of the CTA's patches while the copy is in flight
-    for (int q = w; q < count; q += kStagedWarps) gather_patch<T, 2>(g, d, p0 + q, sd[q], lane);
-    uint32_t done = 0;
-    for (int it = 0; it < kWaitSpins && !done; ++it) done = mbar_try_wait(bar, 0);
-    // block-uniform outcome (also orders the gathered defects before use)
-    if (!__syncthreads_and(done)) {
-        // the copy did not complete in time: record it and wait (bounded) for it before leaving
-        if (tid == 0) atomicExch(&g_wait_timeout, 1);
-        for (int it = 0; it < kWaitSpins && !done; ++it) done = mbar_try_wait(bar, 0);
-        return;
+    // the inverses do not change during a solve: fill the ring before waiting
+    // for the kernel that produces the defect
+    if (tid == 0)
+        for (int64_t k = 0; k < min((int64_t)STAGES, mine); ++k) issue(k);
+    NMG_PDL_ENTRY();
+    for (int k = 0; k < GD; ++k) gather(k);
+    for (int64_t k = 0; k < mine; ++k) {
+        gather(k + GD);            // slot of chunk k - 1, released by the barrier that ended it
+        cp_async_wait<GD>();       // this thread's gather of chunk k has landed
+        const int st = (int)(k % STAGES);
+        uint32_t done = 0;
+        for (int it = 0; it < kWaitSpins && !done; ++it)
+            done = mbar_try_wait(smem_addr(&mbar[st]), (uint32_t)((k / STAGES) & 1));
+        // block-uniform outcome; also publishes the gathered defects of chunk k
+        if (!__syncthreads_and(done)) {
+            cp_async_wait_all();
+            if (tid == 0) {
+                // record the timeout, then wait (bounded) for every copy still in flight
+                atomicExch(&g_wait_timeout, 1);
+                for (int64_t kk = k; kk < min(k + STAGES, mine); ++kk) {
+                    uint32_t ok = 0;
+                    for (int it = 0; it < kWaitSpins && !ok; ++it)
+                        ok = mbar_try_wait(smem_addr(&mbar[kk % STAGES]), (uint32_t)((kk / STAGES) & 1));
+                }
+            }
+            return;
+        }
+        const int64_t p = (blockIdx.x + k * G) * CP + q;
+        if (p < g.patches && lane < 27) {
+            const TS* Ap = ring + st * stage_elems + (int64_t)q * stride;
+            const T* dk = sd[k % (GD + 1)][q];
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) acc = fma(Cvt<T, TS>::f(Ap[j * NP + row]), dk[j], acc);
+            corr[p * NP + row] = acc;
+        }
+        __syncthreads();   // stage st and the defect slot of chunk k are free again
+        if (tid == 0 && k + STAGES < mine) issue(k + STAGES);
     }
-    for (int q = w; q < count; q += kStagedWarps)
-        apply_patch<T, TS, 2, false>(sinv + (int64_t)q * stride, sd[q], corr + (p0 + q) * NP, lane);
+    cp_async_wait_all();
 }
 
 // x += w(node) * sum over the patches that contain the node of their
@@ -205,29 +260,63 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
 }
 
 template <typename TX>
-void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* z64, double* w, cudaStream_t s) {
+void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* Z, int64_t ldz, const int* cyc, double* w,
+                        cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(g.nodes, 256));
-    if (g.dim == 2) pdl_launch(k_spmv_zstore<TX, 2>, grid, dim3(256), 0, s, g, A, xf, z64, w);
-    else pdl_launch(k_spmv_zstore<TX, 3>, grid, dim3(256), 0, s, g, A, xf, z64, w);
+    if (g.dim == 2) pdl_launch(k_spmv_zstore<TX, 2>, grid, dim3(256), 0, s, g, A, xf, Z, ldz, cyc, w);
+    else pdl_launch(k_spmv_zstore<TX, 3>, grid, dim3(256), 0, s, g, A, xf, Z, ldz, cyc, w);
 }
-template void launch_spmv_zstore<float>(const Geom&, const double*, const float*, double*, double*, cudaStream_t);
-template void launch_spmv_zstore<double>(const Geom&, const double*, const double*, double*, double*, cudaStream_t);
+template void launch_spmv_zstore<float>(const Geom&, const double*, const float*, double*, int64_t, const int*,
+                                        double*, cudaStream_t);
+template void launch_spmv_zstore<double>(const Geom&, const double*, const double*, double*, int64_t, const int*,
+                                         double*, cudaStream_t);
+
+// Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
+// resident count comes from the occupancy calculator for the kernel's shared
+// memory (cached per device and kernel instance).
+template <typename T, typename TS, int DIM, int STAGES>
+static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
+    constexpr int CP = DIM == 2 ? 4 : 1;
+    const size_t smem = (size_t)STAGES * CP * stride * sizeof(TS);
+    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int resident[kMaxDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int r = (dev >= 0 && dev < kMaxDevices) ? resident[dev] : 0;
+    if (r <= 0) {
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRingThreads, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        r = std::max(1, per_sm) * std::max(1, sms);
+        if (dev >= 0 && dev < kMaxDevices) resident[dev] = r;
+    }
+    const int64_t chunks = (g.patches + CP - 1) / CP;
+    const dim3 grid((unsigned)std::min<int64_t>(chunks, r));
+    pdl_launch(kern, grid, dim3(kRingThreads), smem, s, g, inv, stride, d, corr);
+}
 
 template <typename T, typename TS>
 void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
     g_launches += 1;
-    // the bulk copy needs 16-byte aligned source chunks; other layouts use the warp kernel
-    const bool aligned = ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
-                         stride <= 27 * 27 + 16 && sizeof(TS) <= 4;   // FP64 keeps the warp kernel
-    if (g.dim == 2 && aligned) {
-        // the stride is at most n_p^2 + 16 elements (padding to 16 bytes)
-        cudaFuncSetAttribute(k_vanka_apply_staged2d<T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)kPPC * (27 * 27 + 16) * sizeof(TS)));
-        const size_t smem = (size_t)kPPC * stride * sizeof(TS);
-        const dim3 grid((unsigned)((g.patches + kPPC - 1) / kPPC));
-        pdl_launch(k_vanka_apply_staged2d<T, TS>, grid, dim3(kStagedWarps * 32), smem, s, g, inv, stride, d, corr);
-    } else if (g.dim == 2) {
+    // the bulk copies need 16-byte aligned chunks and the unpadded column
+    // layout (stride at most n_p^2 rounded up to 16 bytes); FP64 and other
+    // layouts use the warp kernel
+    const int np = g.dim == 2 ? 27 : 108;
+    const bool ring = sizeof(TS) <= 4 && ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
+                      stride >= (int64_t)np * np && stride * (int64_t)sizeof(TS) <= (int64_t)np * np * sizeof(TS) + 16;
+    if (g.patches == 0) return;
+    if constexpr (sizeof(TS) <= 4) {
+        if (ring) {
+            // about 70 KB (2d) / 187 KB (3d) of inverses in flight per CTA
+            constexpr int S2 = sizeof(TS) == 4 ? 6 : 12, S3 = sizeof(TS) == 4 ? 4 : 8;
+            if (g.dim == 2) launch_ring<T, TS, 2, S2>(g, inv, stride, d, corr, s);
+            else launch_ring<T, TS, 3, S3>(g, inv, stride, d, corr, s);
+            return;
+        }
+    }
+    if (g.dim == 2) {
         constexpr int W = 4;
         const dim3 grid((unsigned)((g.patches + W - 1) / W));
         pdl_launch(k_vanka_apply<T, TS, 2, W>, grid, dim3(W * 32), 0, s, g, inv, stride, d, corr);

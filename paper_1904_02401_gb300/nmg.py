@@ -65,6 +65,7 @@ class nmg_solve_opts(C.Structure):
         ("weighting", C.c_int),
         ("use_graph", C.c_int),
         ("engine", C.c_int),
+        ("tail_patches", C.c_int),
     ]
 
 
@@ -77,6 +78,7 @@ class nmg_solve_info(C.Structure):
         ("status", C.c_int),
         ("launches", C.c_int64),
         ("engine", C.c_int),
+        ("device_loop", C.c_int),
     ]
 
 

@@ -212,7 +212,7 @@ def _iteration_tie_ok(gpu_its, ora_its, hist, rtol):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
 def test_solve_fp64_matches_oracle(nmg, built, sessions, case, use_graph):
     s, h = built[case]
     S = sessions[case]
@@ -222,6 +222,7 @@ def test_solve_fp64_matches_oracle(nmg, built, sessions, case, use_graph):
     x = torch.empty_like(b)
     info = S.solve(b, x, precision=0, use_graph=use_graph)
     assert info.status == 0
+    assert info.device_loop == (1 if use_graph == 2 else 0)
     assert _iteration_tie_ok(info.iterations, info_o["iterations"], hist, 1e-8), (info.iterations, info_o)
     xg = host(x)
     assert rel(xg, xo) <= 1e-8
@@ -248,6 +249,38 @@ def test_solve_mixed_precision(nmg, built, sessions, case, prec):
     err_o = rel(xo, xt)
     assert err <= max(1e-7, 20 * err_o), (err, err_o)
     assert info.iterations <= info_o["iterations"] + 3
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("restart,maxit", [(30, 1000), (3, 1000), (4, 6)])
+def test_device_loop_equals_host_steps(nmg, built, sessions, case, prec, restart, maxit):
+    """Restart cycles run as on-device graph loops take the same decisions and
+    produce the same iterate, bit for bit, as cycles stepped by the host
+    (several cycles with restart 3; the iteration limit reached mid-cycle)."""
+    s, _ = built[case]
+    S = sessions[case]
+    b = cu(s.rhs, np.float64)
+    out = []
+    for graph in (1, 2):
+        x = torch.empty_like(b)
+        info = nmg.nmg_solve_info()
+        st = nmg.nmg_solve(S.handle, b, x, _opts(nmg, precision=prec, use_graph=graph, restart=restart, maxit=maxit),
+                           info)
+        out.append((st, info.iterations, info.restarts, info.device_loop, x))
+    (st1, it1, rs1, dl1, x1), (st2, it2, rs2, dl2, x2) = out
+    assert (dl1, dl2) == (0, 1)
+    assert (st1, it1, rs1) == (st2, it2, rs2)
+    assert it1 <= maxit
+    assert st1 == 0 or (st1 == nmg.NMG_ERR_NOT_CONVERGED and it1 == maxit)
+    if maxit == 1000:
+        assert st1 == 0
+    assert torch.equal(x1, x2)
+
+
+def _opts(nmg, **kw):
+    from paper_1904_02401_gb300.session import solve_opts
+    return solve_opts(**kw)
 
 
 def test_solve_host_buffers_and_determinism(nmg, built, sessions):
@@ -310,18 +343,25 @@ def test_error_paths(nmg, built):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("prec", PRECS)
 def test_engines_agree(nmg, built, sessions, case, prec):
-    """One-kernel-per-step (plain and graph), fused and persistent V-cycles run the
-    same element code in the same order: their results are bitwise identical."""
+    """One-kernel-per-step (plain and graph), fused, persistent and cluster-tail
+    V-cycles run the same element code in the same order: their results are
+    bitwise identical.  The tails cover the two coarsest levels, and the whole
+    V-cycle (finest level included, written to the caller's z)."""
     from paper_1904_02401_gb300.session import solve_opts
     s, h = built[case]
     S = sessions[case]
     dt = vdtype(prec)
     r = cu(s.rhs.astype(dt), dt)
+    p1 = int(np.prod([nk // 2 ** (s.problem.levels - 2) // 2 for nk in s.problem.n]))   # patches of level 1
     outs = []
-    for engine, graph in ((nmg.NMG_ENGINE_KERNELS, 0), (nmg.NMG_ENGINE_KERNELS, 1), (nmg.NMG_ENGINE_PERSISTENT, 0),
-                          (nmg.NMG_ENGINE_FUSED, 0), (nmg.NMG_ENGINE_FUSED, 1)):
+    for engine, graph, tail in ((nmg.NMG_ENGINE_KERNELS, 0, 0), (nmg.NMG_ENGINE_KERNELS, 1, 0),
+                                (nmg.NMG_ENGINE_PERSISTENT, 0, 0), (nmg.NMG_ENGINE_FUSED, 0, 0),
+                                (nmg.NMG_ENGINE_FUSED, 1, 0), (nmg.NMG_ENGINE_KERNELS, 0, p1),
+                                (nmg.NMG_ENGINE_FUSED, 1, p1), (nmg.NMG_ENGINE_KERNELS, 1, 1 << 30),
+                                (nmg.NMG_ENGINE_FUSED, 0, 1 << 30)):
         z = torch.zeros_like(r)
-        nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=graph, engine=engine), r, z))
+        o = solve_opts(precision=prec, use_graph=graph, engine=engine, tail_patches=tail)
+        nmg.check(nmg.nmg_vcycle(S.handle, o, r, z))
         outs.append(z)
     for k in range(1, len(outs)):
         assert torch.equal(outs[0], outs[k]), k
