@@ -72,6 +72,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (the replicas'
+    slowest time is the job's time); identity without a process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(world, ms_max):
+    """Solves per second of the whole job: every rank solves its own replica."""
+    return world * 1000.0 / ms_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -306,10 +321,7 @@ def gpu_arm(args):
         e2e.append(1000.0 * (time.perf_counter() - t))
 
     ms = statistics.mean(times)
-    ms_tensor = torch.tensor([ms, wall], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_tensor, op=dist.ReduceOp.MAX)
-    ms_max, wall_max = ms_tensor.tolist()
+    ms_max, wall_max = max_over_ranks([ms, wall], dist, "cuda")
 
     if rank != 0:
         if dist:
@@ -346,7 +358,7 @@ def gpu_arm(args):
         "iterations": infos[-1].iterations,
         "engine": {1: "kernels", 2: "persistent", 3: "fused"}.get(infos[-1].engine, "?"),
         "rel_residual": infos[-1].rel_residual,
-        "solves_per_s": world * 1000.0 / ms_max,
+        "solves_per_s": job_throughput(world, ms_max),
         "p50_ms": statistics.median(times),
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,

@@ -183,14 +183,14 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
     return s_last != 0;
 }
 
-// Multi-dot machinery.  FP64 arithmetic is the scarce resource of these
-// kernels (the FP64 pipe of an SM retires about one FMA per clock), so the
-// reductions are built to spend few FP64 additions: a thread accumulates up to
-// 32 dot products over ~n / 19k elements, a warp reduces its 32 values by a
-// transposing butterfly (31 additions per lane instead of 5 per value), the
-// block adds its warps, and the last block sums the block partials in a fixed
-// order.  Results are bitwise reproducible run to run.
-constexpr int kMdThreads = 64;
+// Multi-dot machinery.  FP64 arithmetic is a scarce resource here (the FP64
+// pipe of an SM retires about two operations per clock), so the reductions
+// spend few FP64 additions: a thread accumulates up to 32 dot products, a warp
+// reduces its 32 values by a transposing butterfly (31 additions per lane
+// instead of 5 per value), the block adds its warps, and the last block sums
+// the block partials in a fixed order.  Results are bitwise reproducible run
+// to run.
+constexpr int kMdThreads = 256;
 constexpr int kMdWarps = kMdThreads / 32;
 constexpr int kMdChunk = 32;   // vectors per pass over w
 
