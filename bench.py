@@ -60,6 +60,8 @@ def parse():
                     help="1: V-cycle graphs with host-stepped FGMRES; 2: also one on-device loop per restart cycle")
     ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent", "fused"],
                     help="V-cycle engine (auto: the autotuner picks it on the first solve)")
+    ap.add_argument("--tail-patches", type=int, default=0,
+                    help="with --engine kernels/fused: levels with at most this many patches run in the cluster tail")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--serving", action="store_true",
                     help="serving workload: Poisson stream of solves over resident 2d/3d hierarchies")
@@ -258,7 +260,7 @@ def gpu_arm(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine)
+                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine, tail_patches=args.tail_patches)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -278,7 +280,8 @@ def gpu_arm(args):
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
-            info = S.solve(b, x, precision=args.precision, use_graph=use_graph, engine=engine)
+            info = S.solve(b, x, precision=args.precision, use_graph=use_graph, engine=engine,
+                           tail_patches=args.tail_patches)
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
         if rank == 0:

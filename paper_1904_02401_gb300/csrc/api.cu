@@ -156,32 +156,51 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
 
 // z = V-cycle(r) on the finest level; b_fine / x_fine are the finest-level
 // right-hand side and result (the level's own buffers when null).
+// Top level of the cluster tail for the current threshold, at most top: the
+// levels 1..c all have at most tail_patches patches and their data fits the
+// shared memory of a cluster (-1: no tail).
+static int tail_top(const Hierarchy* h, int prec, int top) {
+    if (h->tail_patches[prec] <= 0) return -1;
+    int c = -1;
+    for (int l = 0; l <= top && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
+    return c >= 0 ? resident_tail_top(h, prec, c) : -1;
+}
+
+// V-cycle on levels 0..top (b_top / x_top override the top level's buffers):
+// levels above the cluster tail with one kernel per step, the tail (if any)
+// as one cluster launch, else the coarse solve.
 template <typename T>
-static void run_vcycle(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting, const T* b_fine,
-                       T* x_fine) {
-    const int Lc = h->L;
+static void vcycle_levels(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
+                          const T* b_top, T* x_top, bool allow_tail) {
     cudaStream_t s = h->stream;
     const bool avg = weighting == NMG_WEIGHT_AVERAGE;
     const T om = (T)omega;
-    auto bptr = [&](int l) -> T* { return (l == Lc - 1 && b_fine) ? const_cast<T*>(b_fine) : (T*)h->lev[l].p[prec].b; };
-    auto xptr = [&](int l) -> T* { return (l == Lc - 1 && x_fine) ? x_fine : (T*)h->lev[l].p[prec].x; };
-    // levels 0..c (all with at most tail_patches patches) run as one cluster kernel
-    int c = -1;
-    if (h->tail_patches[prec] > 0)
-        for (int l = 0; l < Lc && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
-    for (int l = Lc - 1; l >= 1 && l > c; --l) {
+    auto bptr = [&](int l) -> T* { return (l == top && b_top) ? const_cast<T*>(b_top) : (T*)h->lev[l].p[prec].b; };
+    auto xptr = [&](int l) -> T* { return (l == top && x_top) ? x_top : (T*)h->lev[l].p[prec].x; };
+    const int c = allow_tail ? tail_top(h, prec, top) : -1;
+    for (int l = top; l >= 1 && l > c; --l) {
         Level& L = h->lev[l];
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu1, true, om, avg);
         launch_spmv<T>(L.g, (const T*)L.p[prec].A, xptr(l), bptr(l), (T*)L.p[prec].r, true, s);
         launch_restrict<T>(L.g, h->lev[l - 1].g, (const T*)L.p[prec].r, bptr(l - 1), h->lev[l - 1].mask, s);
     }
-    if (c >= 0) launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, bptr(c), xptr(c));
-    else launch_coarse_gemv<T>(h->coarse_inv, h->n0, bptr(0), xptr(0), s);
-    for (int l = c >= 1 ? c + 1 : 1; l < Lc; ++l) {
+    if (c >= 0) {
+        if (!launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, bptr(c), xptr(c)))
+            vcycle_levels<T>(h, prec, c, nu1, nu2, omega, weighting, bptr(c), xptr(c), false);
+    } else {
+        launch_coarse_gemv<T>(h->coarse_inv, h->n0, bptr(0), xptr(0), s);
+    }
+    for (int l = c >= 1 ? c + 1 : 1; l <= top; ++l) {
         Level& L = h->lev[l];
         launch_prolong_add<T>(L.g, h->lev[l - 1].g, xptr(l - 1), xptr(l), L.mask, s);
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu2, false, om, avg);
     }
+}
+
+template <typename T>
+static void run_vcycle(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting, const T* b_fine,
+                       T* x_fine) {
+    vcycle_levels<T>(h, prec, h->L - 1, nu1, nu2, omega, weighting, b_fine, x_fine, true);
 }
 
 // The same V-cycle on the level buffers with fewer kernels: each Vanka update
@@ -195,9 +214,7 @@ static void run_vcycle_fused(Hierarchy* h, int prec, int nu1, int nu2, double om
     cudaStream_t s = h->stream;
     const bool avg = weighting == NMG_WEIGHT_AVERAGE;
     const T om = (T)omega;
-    int c = -1;
-    if (h->tail_patches[prec] > 0)
-        for (int l = 0; l < Lc && (l == 0 || h->lev[l].g.patches <= h->tail_patches[prec]); ++l) c = l;
+    const int c = tail_top(h, prec, Lc - 1);
     T* cur_level[kMaxLevels] = {};
     auto apply = [&](int l, const T* d) {
         PrecData& P = h->lev[l].p[prec];
@@ -240,8 +257,12 @@ static void run_vcycle_fused(Hierarchy* h, int prec, int nu1, int nu2, double om
         }
         cur_level[l] = const_cast<T*>(cur);
     }
-    if (c >= 0) launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, nullptr, nullptr);
-    else launch_coarse_gemv<T>(h->coarse_inv, h->n0, (const T*)h->lev[0].p[prec].b, (T*)h->lev[0].p[prec].x, s);
+    if (c >= 0) {
+        if (!launch_vcycle_tail(h, prec, c, nu1, nu2, omega, weighting, nullptr, nullptr))
+            vcycle_levels<T>(h, prec, c, nu1, nu2, omega, weighting, nullptr, nullptr, false);
+    } else {
+        launch_coarse_gemv<T>(h->coarse_inv, h->n0, (const T*)h->lev[0].p[prec].b, (T*)h->lev[0].p[prec].x, s);
+    }
     for (int l = c >= 1 ? c + 1 : 1; l < Lc; ++l) {
         Level& L = h->lev[l];
         PrecData& P = L.p[prec];
@@ -400,9 +421,8 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     std::vector<Cand> cands;
     int last_level = -2;
     for (int tail : {0, 64, 256, 1024, 4096}) {
-        int c = -1;
-        if (tail > 0)
-            for (int l = 0; l < h->L && (l == 0 || h->lev[l].g.patches <= tail); ++l) c = l;
+        h->tail_patches[prec] = tail;
+        const int c = tail_top(h, prec, h->L - 1);
         if (c != last_level)
             for (int fz : {0, 1}) cands.push_back({fz ? NMG_ENGINE_FUSED : NMG_ENGINE_KERNELS, tail, fz});
         last_level = c;

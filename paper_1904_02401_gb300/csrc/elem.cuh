@@ -18,17 +18,24 @@ template <> struct Cvt<float, __nv_bfloat16> {
 template <typename TS> __device__ __forceinline__ TS ldg(const TS* p) { return __ldg(p); }
 template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) { return *p; }
 
+// Index arithmetic in 32 bits (node and patch counts stay below 2^31; 64-bit
+// division is a long emulated sequence on the critical path of small levels).
 __device__ __forceinline__ void node_xyz(const Geom& g, int64_t i, int& x, int& y, int& z) {
-    x = (int)(i % g.nn[0]);
-    int64_t t = i / g.nn[0];
-    y = (int)(t % g.nn[1]);
-    z = (int)(t / g.nn[1]);
+    const uint32_t ii = (uint32_t)i, n0 = (uint32_t)g.nn[0], n1 = (uint32_t)g.nn[1];
+    const uint32_t t = ii / n0;
+    x = (int)(ii - t * n0);
+    const uint32_t u = t / n1;
+    y = (int)(t - u * n1);
+    z = (int)u;
 }
 
 __device__ __forceinline__ void patch_xyz(const Geom& g, int64_t p, int& px, int& py, int& pz) {
-    px = (int)(p % g.pc[0]);
-    py = (int)((p / g.pc[0]) % g.pc[1]);
-    pz = (int)(p / ((int64_t)g.pc[0] * g.pc[1]));
+    const uint32_t pp = (uint32_t)p, c0 = (uint32_t)g.pc[0], c1 = (uint32_t)g.pc[1];
+    const uint32_t t = pp / c0;
+    px = (int)(pp - t * c0);
+    const uint32_t u = t / c1;
+    py = (int)(t - u * c1);
+    pz = (int)u;
 }
 
 __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int pz, int an) {
@@ -38,7 +45,7 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
 
 // y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
 // at a node j come from xval(j, xv) (loaded, converted or recomputed).
-template <typename T, int DIM, class XF>
+template <typename T, int DIM, class XF, bool GLOBAL_A = true>
 __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
                                             const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     constexpr int NC = DIM + 1;
@@ -63,24 +70,29 @@ __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__
 #pragma unroll
             for (int r = 0; r < NC; ++r)
 #pragma unroll
-                for (int c = 0; c < NC; ++c) acc[r] = fma(__ldg(As + (int64_t)(r * NC + c) * g.ld), xv[c], acc[r]);
+                for (int c = 0; c < NC; ++c) {
+                    const T* a = As + (int64_t)(r * NC + c) * g.ld;
+                    T av;
+                    if constexpr (GLOBAL_A) av = __ldg(a);
+                    else av = *a;
+                    acc[r] = fma(av, xv[c], acc[r]);
+                }
         }
     }
 #pragma unroll
     for (int r = 0; r < NC; ++r) y[i * NC + r] = residual ? b[i * NC + r] - acc[r] : acc[r];
 }
 
-// y_i = (A x)_i or b_i - (A x)_i with x stored as TX (converted to T on load).
-template <typename T, int DIM, typename TX = T>
+// y_i = (A x)_i or b_i - (A x)_i with x stored as TX (converted to T on load);
+// GLOBAL_A = false when A lives in shared memory.
+template <typename T, int DIM, typename TX = T, bool GLOBAL_A = true>
 __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const TX* __restrict__ x,
                                           const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
-    spmv_node_f<T, DIM>(
-        g, A,
-        [&](int64_t j, T* xv) {
+    auto xval = [&](int64_t j, T* xv) {
 #pragma unroll
-            for (int c = 0; c < DIM + 1; ++c) xv[c] = (T)x[j * (DIM + 1) + c];
-        },
-        b, y, residual, i);
+        for (int c = 0; c < DIM + 1; ++c) xv[c] = (T)x[j * (DIM + 1) + c];
+    };
+    spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A>(g, A, xval, b, y, residual, i);
 }
 
 // Gathers R_p d into sd[0..NP) (called by one warp; lane-strided).

@@ -130,9 +130,12 @@ enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_AB
 struct Hierarchy;
 cudaError_t launch_vcycle_persistent(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting,
                                      unsigned* bar, int* abort, int small_patches);
-// Levels 0..top of a V-cycle as one thread-block-cluster launch (cluster.cu).
-void launch_vcycle_tail(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
+// Levels 0..top of a V-cycle as one thread-block-cluster launch with the
+// levels resident in shared memory (cluster.cu); false if no cluster can hold
+// them.  resident_tail_top: the largest top <= want that fits (-1: none).
+bool launch_vcycle_tail(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
                         const void* b_top, void* x_top);
+int resident_tail_top(const Hierarchy* h, int prec, int want);
 
 // ---------------------------------------------------------------------------
 // Launchers (setup_kernels.cu)

@@ -22,7 +22,7 @@ constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CT
 
 // y = A x  or  y = b - A x, one thread per node.  A in stencil layout.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
        T* __restrict__ y, bool residual) {
     NMG_PDL_ENTRY();
@@ -34,7 +34,7 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
 // written, converted, to Z_j (the FGMRES basis vector of step j = cyc[0]):
 // the outer product of one FGMRES iteration without a separate conversion pass.
 template <typename TX, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ Z, int64_t ldz,
               const int* __restrict__ cyc, double* __restrict__ w) {
     NMG_PDL_ENTRY();
@@ -53,7 +53,7 @@ k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, d
 // them by the broadcast d_j from shared memory; no cross-lane reduction.
 // Used for 3d patches (n_p = 108), where each warp streams 46.7 KB.
 template <typename T, typename TS, int DIM, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, 1)
 k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
               T* __restrict__ corr) {
     NMG_PDL_ENTRY();
@@ -78,7 +78,7 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 // ascending order with one fma per term, as in apply_patch, so the
 // corrections equal those of the other apply kernels bit for bit.
 template <typename T, typename TS, int DIM, int STAGES>
-__global__ void __launch_bounds__(kRingThreads)
+__global__ void __launch_bounds__(kRingThreads, 1)
 k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
                    T* __restrict__ corr) {
     constexpr int NC = DIM + 1;
@@ -162,7 +162,7 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
 // corrections (fixed order: ascending patch index), w = omega / multiplicity
 // ("average") or omega ("sum").  One thread per node, no atomics.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_vanka_update(Geom g, const T* __restrict__ corr, const T* x_in, T* x_out, bool x_zero, T omega,
                bool average) {
     NMG_PDL_ENTRY();
@@ -173,7 +173,7 @@ k_vanka_update(Geom g, const T* __restrict__ corr, const T* x_in, T* x_out, bool
 // Fused Vanka update and residual: x_out = x_in + w * corrections, r = b - A x_out
 // (x_out at the neighbours recomputed from x_in and the corrections).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_update_residual(Geom g, const T* __restrict__ A, const T* __restrict__ corr, const T* __restrict__ x_in,
                   bool x_zero, T omega, bool average, const T* __restrict__ b, T* __restrict__ x_out,
                   T* __restrict__ r) {
@@ -184,7 +184,7 @@ k_update_residual(Geom g, const T* __restrict__ A, const T* __restrict__ corr, c
 
 // Fused prolongation and residual: x_out = x_in + P e_c, r = b - A x_out.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_prolong_residual(Geom f, Geom c, const T* __restrict__ A, const T* __restrict__ ec, const T* __restrict__ x_in,
                    const uint8_t* __restrict__ fmask, const T* __restrict__ b, T* __restrict__ x_out,
                    T* __restrict__ r) {
@@ -195,7 +195,7 @@ k_prolong_residual(Geom f, Geom c, const T* __restrict__ A, const T* __restrict_
 
 // r_c = P^T r_f (Q1 full weighting), coarse Dirichlet entries zero.  One thread per coarse node.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_restrict(Geom f, Geom c, const T* __restrict__ rf, T* __restrict__ rc, const uint8_t* __restrict__ cmask) {
     NMG_PDL_ENTRY();
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -204,7 +204,7 @@ k_restrict(Geom f, Geom c, const T* __restrict__ rf, T* __restrict__ rc, const u
 
 // x_f += P e_c (Q1 interpolation), fine Dirichlet entries untouched.  One thread per fine node.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_prolong_add(Geom f, Geom c, const T* __restrict__ ec, T* __restrict__ xf, const uint8_t* __restrict__ fmask) {
     NMG_PDL_ENTRY();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -213,7 +213,7 @@ k_prolong_add(Geom f, Geom c, const T* __restrict__ ec, T* __restrict__ xf, cons
 
 // x = inv * b with the FP64 dense coarse inverse, one warp per row, FP64 sums.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_coarse_gemv(const double* __restrict__ inv, int64_t n, const T* __restrict__ b, T* __restrict__ x) {
     NMG_PDL_ENTRY();
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
