@@ -41,8 +41,8 @@ WORKLOADS = {
 # capture of the current kernel source (profiles/k_vanka_apply_*.md); a
 # workload or precision without a capture of the current source reports null.
 PROFILED_TRAFFIC = {
-    ("cfg2", 1): 48_784_896 + 26_880,       # k_vanka_apply_staged2d, 2d 256x256, FP32
-    ("cfg3", 1): 191_955_712 + 3_209_728,   # k_vanka_apply<float,float,3,4>, 3d 32^3, FP32
+    ("cfg2", 1): 48_782_336 + 8_448,        # k_vanka_apply_ring<float,float,2,6>, 2d 256x256, FP32
+    ("cfg3", 1): 191_705_600 + 3_771_648,   # k_vanka_apply_ring<float,float,3,4>, 3d 32^3, FP32
 }
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
@@ -366,7 +366,7 @@ def gpu_arm(args):
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
                       "speedup_of_mixed": statistics.mean(t64) / ms},
-        "roofline": {"kernel": ("k_vanka_apply_staged2d" if sysm.problem.dim == 2 else "k_vanka_apply") +
+        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 else "k_vanka_apply_ring") +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
