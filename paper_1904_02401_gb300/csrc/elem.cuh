@@ -15,6 +15,33 @@ template <> struct Cvt<float, __nv_bfloat16> {
     static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 
+// Exact float -> double widening with integer instructions (GB300 retires
+// about two FP64 operations per SM clock, so conversions on the FP64 pipe are
+// not free): the same value as a conversion instruction for zeros, normal and
+// subnormal numbers and infinities (IEEE 754 binary32 -> binary64 field
+// mapping: exponent rebias by 1023 - 127, fraction shifted left by 29).
+__device__ __forceinline__ double widen_exact(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    const uint32_t e = (u >> 23) & 0xffu;
+    uint32_t m = u & 0x7fffffu;
+    uint64_t bits;
+    if (e - 1u < 0xfeu) {                                   // normal
+        bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    } else if (e == 0xffu) {                                // infinity, NaN
+        bits = sign | (0x7ffull << 52) | ((uint64_t)m << 29);
+    } else if (m == 0u) {                                   // zero
+        bits = sign;
+    } else {                                                // subnormal: normalise
+        const int sh = __clz((int)m) - 8;                   // moves the leading one to bit 23
+        m = (m << sh) & 0x7fffffu;
+        bits = sign | ((uint64_t)(897 - sh) << 52) | ((uint64_t)m << 29);
+    }
+    return __longlong_as_double((long long)bits);
+}
+template <typename T, typename TX> __device__ __forceinline__ T widen(TX v) { return (T)v; }
+template <> __device__ __forceinline__ double widen<double, float>(float v) { return widen_exact(v); }
+
 template <typename TS> __device__ __forceinline__ TS ldg(const TS* p) { return __ldg(p); }
 template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) { return *p; }
 
@@ -90,7 +117,7 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
                                           const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     auto xval = [&](int64_t j, T* xv) {
 #pragma unroll
-        for (int c = 0; c < DIM + 1; ++c) xv[c] = (T)x[j * (DIM + 1) + c];
+        for (int c = 0; c < DIM + 1; ++c) xv[c] = widen<T, TX>(x[j * (DIM + 1) + c]);
     };
     spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A>(g, A, xval, b, y, residual, i);
 }

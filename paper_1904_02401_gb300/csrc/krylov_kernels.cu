@@ -194,10 +194,15 @@ constexpr int kMdThreads = 256;
 constexpr int kMdWarps = kMdThreads / 32;
 constexpr int kMdChunk = 32;   // vectors per pass over w
 
-// After the call lane l holds the warp's total of a[l].
-__device__ __forceinline__ double butterfly32(double (&a)[kMdChunk], int lane) {
+// Warp reduction of W per-lane values (W a power of two <= 32): a
+// transposing butterfly over the offsets W/2 .. 1 (W - 1 additions per lane)
+// leaves lane l with the sum of a[l % W] over the 32 / W lanes of its group,
+// and the offsets W .. 16 complete it.  Afterwards lane l holds the warp's
+// total of a[l % W].
+template <int W>
+__device__ __forceinline__ double butterfly(double (&a)[W], int lane) {
 #pragma unroll
-    for (int c = kMdChunk / 2; c >= 1; c >>= 1) {
+    for (int c = W / 2; c >= 1; c >>= 1) {
         const bool upper = (lane & c) != 0;
 #pragma unroll
         for (int q = 0; q < c; ++q) {
@@ -206,22 +211,65 @@ __device__ __forceinline__ double butterfly32(double (&a)[kMdChunk], int lane) {
             a[q] = keep + __shfl_xor_sync(0xffffffffu, send, c);
         }
     }
-    return a[0];
+    double v = a[0];
+#pragma unroll
+    for (int off = W; off < 32; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
-// Block total of the chunk's 32 values -> partial[(chunk * grid + block) * 32 + l].
-__device__ __forceinline__ void block_partials(double (&acc)[kMdChunk], double* __restrict__ partial, int chunk,
-                                               int lane, int warp) {
+// Block totals of the W values -> partial[(chunk * grid + block) * 32 + l], l < W.
+template <int W>
+__device__ __forceinline__ void block_partials(double (&acc)[W], double* __restrict__ partial, int chunk, int lane,
+                                               int warp) {
     __shared__ double red[kMdWarps][kMdChunk];
-    red[warp][lane] = butterfly32(acc, lane);
+    const double v = butterfly<W>(acc, lane);
+    if (lane < W) red[warp][lane] = v;
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && lane < W) {
         double t = red[0][lane];
 #pragma unroll
         for (int ww = 1; ww < kMdWarps; ++ww) t += red[ww][lane];
         partial[((int64_t)chunk * gridDim.x + blockIdx.x) * kMdChunk + lane] = t;
     }
     __syncthreads();
+}
+
+// acc[k] = sum over this thread's elements of V_{c0+k} . w for k < W (columns
+// at or beyond c0 + nv contribute zeros: they are not read).
+template <int W>
+__device__ __forceinline__ void dots(const double* __restrict__ V, int64_t ldv, int c0, int nv,
+                                     const double* __restrict__ w, int64_t n, double (&acc)[W]) {
+    const int64_t T = (int64_t)gridDim.x * kMdThreads;
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[k] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const double v = k < nv ? V[(int64_t)(c0 + k) * ldv + i] : 0.0;
+            acc[k] = fma(v, wi, acc[k]);
+        }
+    }
+}
+
+// One chunk of at most 32 dot products, with the accumulator width the
+// smallest power of two >= nv (FP64 work not spent on absent vectors).
+__device__ __forceinline__ void dots_chunk(const double* __restrict__ V, int64_t ldv, int c0, int nv,
+                                           const double* __restrict__ w, int64_t n, double* __restrict__ partial,
+                                           int chunk, int lane, int warp) {
+#define NMG_DOTS(W)                                        \
+    {                                                      \
+        double acc[W];                                     \
+        dots<W>(V, ldv, c0, nv, w, n, acc);                \
+        block_partials<W>(acc, partial, chunk, lane, warp); \
+    }
+    if (nv > 16) NMG_DOTS(32)
+    else if (nv > 8) NMG_DOTS(16)
+    else if (nv > 4) NMG_DOTS(8)
+    else if (nv > 2) NMG_DOTS(4)
+    else if (nv > 1) NMG_DOTS(2)
+    else NMG_DOTS(1)
+#undef NMG_DOTS
 }
 
 // In the last block: out[k] = sum over the blocks of the partials of value k
@@ -262,20 +310,8 @@ k_multidot_fused(const double* __restrict__ V, int64_t ldv, const int* __restric
     NMG_PDL_ENTRY();
     const int nvec = cyc[0] + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t T = (int64_t)gridDim.x * kMdThreads;
-    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
-        const int nv = min(kMdChunk, nvec - c0);
-        double acc[kMdChunk];
-#pragma unroll
-        for (int k = 0; k < kMdChunk; ++k) acc[k] = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
-            const double wi = w[i];
-#pragma unroll
-            for (int k = 0; k < kMdChunk; ++k)
-                if (k < nv) acc[k] = fma(V[(int64_t)(c0 + k) * ldv + i], wi, acc[k]);
-        }
-        block_partials(acc, partial, chunk, lane, warp);
-    }
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk)
+        dots_chunk(V, ldv, c0, min(kMdChunk, nvec - c0), w, n, partial, chunk, lane, warp);
     if (!last_block(counter)) return;
     finish_chunks(partial, nvec, out, lane, warp);
 }
@@ -294,24 +330,15 @@ k_gs_update_dot(const double* __restrict__ V, int64_t ldv, const int* __restrict
     for (int k = threadIdx.x; k < nvec; k += kMdThreads) hs[k] = h[k];
     __syncthreads();
     const int64_t T = (int64_t)gridDim.x * kMdThreads;
-    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
-        const int nv = min(kMdChunk, nvec - c0);
-        double acc[kMdChunk];
-#pragma unroll
-        for (int k = 0; k < kMdChunk; ++k) acc[k] = 0.0;
-        for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
-            double v = w[i];
-            if (chunk == 0) {
+    for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
+        double v = w[i];
 #pragma unroll 8
-                for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
-                w[i] = v;
-            }
-#pragma unroll
-            for (int k = 0; k < kMdChunk; ++k)
-                if (k < nv) acc[k] = fma(V[(int64_t)(c0 + k) * ldv + i], v, acc[k]);
-        }
-        block_partials(acc, partial, chunk, lane, warp);
+        for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
+        w[i] = v;
     }
+    // this thread reads back only the elements it wrote
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk)
+        dots_chunk(V, ldv, c0, min(kMdChunk, nvec - c0), w, n, partial, chunk, lane, warp);
     if (!last_block(counter)) return;
     finish_chunks(partial, nvec, out, lane, warp);
 }

@@ -43,7 +43,7 @@ k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, d
     if (i >= g.nodes) return;
     double* z64 = Z + (int64_t)cyc[0] * ldz;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) z64[i * NC + c] = (double)xf[i * NC + c];
+    for (int c = 0; c < NC; ++c) z64[i * NC + c] = widen<double, TX>(xf[i * NC + c]);
     spmv_node<double, DIM, TX>(g, A, xf, nullptr, w, false, i);
 }
 
