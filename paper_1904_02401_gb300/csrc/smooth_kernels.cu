@@ -17,7 +17,6 @@ namespace {
 using namespace elem;
 
 constexpr int kWaitSpins = 1 << 22;
-constexpr int kRingThreads = 128;   // 4 warps: 4 x 27 rows of patch inverse per chunk
 constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CTA
 
 // y = A x  or  y = b - A x, one thread per node.  A in stencil layout.
@@ -69,22 +68,22 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 
 // Streaming apply for FP32 / BF16 inverses (2d and 3d): a persistent grid of
 // a few CTAs per SM walks the chunks c = blockIdx.x + k * gridDim.x; a chunk
-// is 4 patches in 2d (one warp per patch) or 1 patch in 3d (4 warps of 27
-// rows each), i.e. 4 x 27 rows in both.  Each CTA keeps STAGES chunk copies
+// is one patch per warp in 2d, or one patch per 4 warps (27 rows each) in 3d,
+// i.e. THREADS / 32 x 27 rows.  Each CTA keeps STAGES chunk copies
 // of inverses (TMA bulk copies completing on one mbarrier per stage) and the
 // defect gathers of kGatherDepth chunks (cp.async) in flight, so neither the
 // DRAM queue nor the gather latency depends on how many warps are resident,
 // and there is no tail wave.  Row i of a patch is summed over the columns j in
 // ascending order with one fma per term, as in apply_patch, so the
 // corrections equal those of the other apply kernels bit for bit.
-template <typename T, typename TS, int DIM, int STAGES>
-__global__ void __launch_bounds__(kRingThreads, 1)
+template <typename T, typename TS, int DIM, int STAGES, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
                    T* __restrict__ corr) {
     constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     constexpr int RW = NP / 27;                    // warps per patch
-    constexpr int CP = (kRingThreads / 32) / RW;   // patches per chunk
+    constexpr int CP = (THREADS / 32) / RW;   // patches per chunk
     constexpr int GD = kGatherDepth;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[STAGES];
@@ -275,11 +274,11 @@ template void launch_spmv_zstore<double>(const Geom&, const double*, const doubl
 // Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
 // resident count comes from the occupancy calculator for the kernel's shared
 // memory (cached per device and kernel instance).
-template <typename T, typename TS, int DIM, int STAGES>
+template <typename T, typename TS, int DIM, int STAGES, int THREADS>
 static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
-    constexpr int CP = DIM == 2 ? 4 : 1;
+    constexpr int CP = (THREADS / 32) / (DIM == 2 ? 1 : 4);
     const size_t smem = (size_t)STAGES * CP * stride * sizeof(TS);
-    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES>;
+    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     static int resident[kMaxDevices] = {};
     int dev = 0;
@@ -287,14 +286,14 @@ static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d
     int r = (dev >= 0 && dev < kMaxDevices) ? resident[dev] : 0;
     if (r <= 0) {
         int per_sm = 0, sms = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRingThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         r = std::max(1, per_sm) * std::max(1, sms);
         if (dev >= 0 && dev < kMaxDevices) resident[dev] = r;
     }
     const int64_t chunks = (g.patches + CP - 1) / CP;
     const dim3 grid((unsigned)std::min<int64_t>(chunks, r));
-    pdl_launch(kern, grid, dim3(kRingThreads), smem, s, g, inv, stride, d, corr);
+    pdl_launch(kern, grid, dim3(THREADS), smem, s, g, inv, stride, d, corr);
 }
 
 template <typename T, typename TS>
@@ -309,10 +308,13 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     if (g.patches == 0) return;
     if constexpr (sizeof(TS) <= 4) {
         if (ring) {
-            // about 70 KB (2d) / 187 KB (3d) of inverses in flight per CTA
-            constexpr int S2 = sizeof(TS) == 4 ? 6 : 12, S3 = sizeof(TS) == 4 ? 4 : 8;
-            if (g.dim == 2) launch_ring<T, TS, 2, S2>(g, inv, stride, d, corr, s);
-            else launch_ring<T, TS, 3, S3>(g, inv, stride, d, corr, s);
+            // about 70 KB (2d, 3 CTAs per SM) / 187 KB (3d, one CTA per SM) of
+            // inverses in flight per CTA; 3d BF16 chunks hold two patches (8
+            // warps), so that the apply of a chunk keeps pace with its copy
+            constexpr int S2 = sizeof(TS) == 4 ? 6 : 12;
+            if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s);
+            else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s);
+            else launch_ring<T, TS, 3, 4, 256>(g, inv, stride, d, corr, s);
             return;
         }
     }
