@@ -444,7 +444,8 @@ def serving_arm(args):
             del sy
     setup_s = time.time() - t0
     rng = np.random.default_rng(2)
-    opts = solve_opts(precision=nmg.NMG_PREC_FP32, engine=nmg.NMG_ENGINE_KERNELS)
+    opts = solve_opts(precision=nmg.NMG_PREC_FP32, engine=nmg.NMG_ENGINE_KERNELS,
+                      use_graph=0 if args.no_graph else args.graph)
     budget = 150 * 10**9
 
     def make_requests(count, seed0):

@@ -122,6 +122,35 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
     spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A>(g, A, xval, b, y, residual, i);
 }
 
+// Row r of node i of y = A x or b - A x: the same terms in the same order as
+// row r of spmv_node (stencil positions ascending, then block columns), so the
+// value is bitwise equal; lets a kernel spread a node's rows over threads.
+template <typename T, int DIM>
+__device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
+                                         const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i,
+                                         int r) {
+    constexpr int NC = DIM + 1;
+    constexpr int NB = NC * NC;
+    constexpr int NST = (DIM == 2) ? 9 : 27;
+    int ix, iy, iz;
+    node_xyz(g, i, ix, iy, iz);
+    const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
+    T acc = T(0);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) {
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+        const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                        (iz + dz >= 0) && (iz + dz < g.nn[2]);
+        if (ok) {
+            const int64_t j = i + dx + dy * sy + dz * sz;
+            const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), x[j * NC + c], acc);
+        }
+    }
+    y[i * NC + r] = residual ? b[i * NC + r] - acc : acc;
+}
+
 // Gathers R_p d into sd[0..NP) (called by one warp; lane-strided).
 template <typename T, int DIM>
 __device__ __forceinline__ void gather_patch(const Geom& g, const T* __restrict__ d, int64_t p, T* sd, int lane) {

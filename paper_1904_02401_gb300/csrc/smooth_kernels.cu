@@ -29,6 +29,23 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
     if (i < g.nodes) spmv_node<T, DIM>(g, A, x, b, y, residual, i);
 }
 
+// The same product with one thread per (block row, node): thread t computes
+// row r = t / nodes of node t % nodes, so a warp still reads one contiguous
+// segment of each stencil array while a node's rows run in parallel.  Faster
+// where a node's row work is long (3d: 108 terms per row; FP64), slower for
+// the 2d FP32 product, whose extra reads of x cost more than the added
+// parallelism gains.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256, 1)
+k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
+            T* __restrict__ y, bool residual) {
+    NMG_PDL_ENTRY();
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= g.nodes * (DIM + 1)) return;
+    const uint32_t nodes = (uint32_t)g.nodes, r = (uint32_t)t / nodes;
+    spmv_row<T, DIM>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
+}
+
 // w = A z in FP64 with z read from the V-cycle output xf (stored as TX) and
 // written, converted, to Z_j (the FGMRES basis vector of step j = cyc[0]):
 // the outer product of one FGMRES iteration without a separate conversion pass.
@@ -253,9 +270,12 @@ cudaError_t wait_timeout_clear(cudaStream_t s) {
 template <typename T>
 void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual, cudaStream_t s) {
     g_launches += 1;
-    const dim3 grid(blocks_for(g.nodes, 256));
-    if (g.dim == 2) pdl_launch(k_spmv<T, 2>, grid, dim3(256), 0, s, g, A, x, b, y, residual);
-    else pdl_launch(k_spmv<T, 3>, grid, dim3(256), 0, s, g, A, x, b, y, residual);
+    if (g.dim == 3)
+        pdl_launch(k_spmv_rows<T, 3>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
+    else if (sizeof(T) == 8)
+        pdl_launch(k_spmv_rows<T, 2>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
+    else
+        pdl_launch(k_spmv<T, 2>, dim3(blocks_for(g.nodes, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
 }
 
 template <typename TX>
