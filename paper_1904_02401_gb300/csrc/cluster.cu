@@ -200,29 +200,58 @@ struct ResidentVCycle {
     }
 
     // Stages the read-only data (owned matrix rows and patch inverses, masks)
-    // into shared memory.
+    // into shared memory; every thread keeps 8 loads in flight.
+    // dst[dix(k)] = src(k) for k < count
+    template <typename E, class SRC, class DIX>
+    __device__ void stage(E* dst, int64_t count, SRC&& src, DIX&& dix) {
+        constexpr int U = 8;
+        for (int64_t k0 = threadIdx.x; k0 < count; k0 += (int64_t)U * blockDim.x) {
+            E v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + (int64_t)u * blockDim.x;
+                if (k < count) v[u] = src(k);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + (int64_t)u * blockDim.x;
+                if (k < count) dst[dix(k)] = v[u];
+            }
+        }
+    }
+    template <typename E, class SRC>
+    __device__ void stage(E* dst, int64_t count, SRC&& src) {
+        stage(dst, count, src, [](int64_t k) { return k; });
+    }
+
     __device__ void load_constants() {
         constexpr int NA = ((DIM == 2) ? 9 : 27) * NC * NC;
         for (int l = 0; l < a.L; ++l) {
             const RLevel& L = a.lev[l];
-            uint8_t* m = reinterpret_cast<uint8_t*>(sm + L.o_mask);
-            for (int64_t i = threadIdx.x; i < L.g.nodes * NC; i += blockDim.x) m[i] = L.mask[i];
+            stage(reinterpret_cast<uint8_t*>(sm + L.o_mask), L.g.nodes * NC, [&](int64_t k) { return L.mask[k]; });
             if (l == 0) continue;
             int64_t lo, hi;
             own_range(L.g.nodes, L.node_chunk, rank, lo, hi);
-            const int64_t cnt = hi - lo;
+            const uint32_t cnt = (uint32_t)(hi - lo);
             const T* A = reinterpret_cast<const T*>(L.A);
-            T* As = vec(L.o_A);
-            if (cnt > 0)
-                for (uint32_t k = threadIdx.x; k < (uint32_t)(NA * cnt); k += blockDim.x) {
-                    const uint32_t s = k / (uint32_t)cnt, j = k - s * (uint32_t)cnt;
-                    As[s * L.node_chunk + j] = A[s * L.g.ld + lo + j];
-                }
+            if (cnt > 0) {
+                // As[s * node_chunk + j] = A[s * ld + lo + j], s < NA, j < cnt
+                const int nch = L.node_chunk;
+                const int64_t ld = L.g.ld;
+                stage(vec(L.o_A), (int64_t)NA * cnt,
+                      [&](int64_t k) {
+                          const uint32_t s = (uint32_t)k / cnt;
+                          return A[s * ld + lo + ((uint32_t)k - s * cnt)];
+                      },
+                      [&](int64_t k) {
+                          const uint32_t s = (uint32_t)k / cnt;
+                          return (int64_t)s * nch + ((uint32_t)k - s * cnt);
+                      });
+            }
             int64_t plo, phi;
             own_range(L.g.patches, L.patch_chunk, rank, plo, phi);
             const TS* inv = reinterpret_cast<const TS*>(L.inv) + plo * L.stride;
-            TS* si = reinterpret_cast<TS*>(sm + L.o_inv);
-            for (int64_t k = threadIdx.x; k < (phi - plo) * L.stride; k += blockDim.x) si[k] = inv[k];
+            stage(reinterpret_cast<TS*>(sm + L.o_inv), (phi - plo) * L.stride, [&](int64_t k) { return inv[k]; });
         }
     }
 
@@ -230,7 +259,7 @@ struct ResidentVCycle {
     __device__ void load_rhs() {
         const RLevel& L = a.lev[a.L - 1];
         const T* b = reinterpret_cast<const T*>(a.b_top);
-        for (int64_t i = threadIdx.x; i < L.g.nodes * NC; i += blockDim.x) vec(L.o_b)[i] = b[i];
+        stage(vec(L.o_b), L.g.nodes * NC, [&](int64_t k) { return b[k]; });
     }
 
     // The CTA's owned entries of the top level's result, to global memory.
