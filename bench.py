@@ -307,8 +307,8 @@ def gpu_arm(args):
     # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
     ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
     _, _, vprof = timed_solves(args.precision, args.steps, min(use_graph, 1), profile=1)
-    rep = C.create_string_buffer(8192)
-    nmg.check(nmg.nmg_autotune_report(S.handle, rep, 8192))
+    rep = C.create_string_buffer(32768)
+    nmg.check(nmg.nmg_autotune_report(S.handle, rep, 32768))
     # plain FP64 path on the same mesh
     t64, i64, _ = timed_solves(nmg.NMG_PREC_FP64, args.steps, use_graph)
 

@@ -98,6 +98,11 @@ typedef struct {
     int tail_patches; /* engines KERNELS and FUSED: the coarse level and every level with at most
                          this many patches run as one thread-block-cluster kernel (0 = none);
                          AUTO picks it itself, PERSISTENT ignores it                              */
+    int tile_patches; /* engine KERNELS: every level above the cluster tail with at most this many
+                         patches runs each Vanka step as one tile-fused kernel (a CTA per tile of
+                         patches recomputes the previous update and the defect on its halo, then
+                         solves its patches; 0 = none); AUTO picks it itself, the other engines
+                         ignore it.  Results are bitwise those of the one-kernel-per-pass path     */
 } nmg_solve_opts;
 
 /* V-cycle execution engines (same arithmetic, same results). */
@@ -120,7 +125,7 @@ typedef struct {
 } nmg_solve_info;
 
 /* Fills *opts with rtol 1e-8, restart 30, maxit 1000, nu1 = nu2 = 2, omega 0.8,
- * precision FP32, weighting AVERAGE, use_graph 2, engine AUTO, tail_patches 0. */
+ * precision FP32, weighting AVERAGE, use_graph 2, engine AUTO, tail_patches 0, tile_patches 0. */
 nmg_status nmg_default_opts(nmg_solve_opts* opts);
 
 /* Creates an empty hierarchy for the mesh in *desc (Section 4.3 (II): nested

@@ -166,9 +166,95 @@ static int tail_top(const Hierarchy* h, int prec, int top) {
     return c >= 0 ? resident_tail_top(h, prec, c) : -1;
 }
 
+// True when level l (above the cluster tail top c) runs tile-fused steps.
+static bool tile_level(const Hierarchy* h, int prec, int l, int c) {
+    return l >= 1 && l > c && h->tile_patches[prec] > 0 && h->lev[l].g.patches <= h->tile_patches[prec];
+}
+
+// One tile-fused launch on level l (tile_kernels.cu) in the level's precision.
+template <typename T>
+static void tile_launch(Hierarchy* h, int l, int prec, int mode, const T* b, const T* x_in, bool x_zero,
+                        const T* corr_in, const T* ec, T* x_out, T* corr_out, T* rc, T omega, bool avg) {
+    Level& L = h->lev[l];
+    PrecData& P = L.p[prec];
+    const Geom& gc = h->lev[l - 1].g;
+    const uint8_t* cmask = h->lev[l - 1].mask;
+    if constexpr (sizeof(T) == 8) {
+        launch_tile_step<double, double>(L.g, gc, mode, (const double*)P.A, (const double*)P.inv, P.inv_stride, b,
+                                         x_in, x_zero, corr_in, ec, L.mask, cmask, x_out, corr_out, rc, omega, avg,
+                                         h->stream);
+    } else if (prec == NMG_PREC_FP32) {
+        launch_tile_step<float, float>(L.g, gc, mode, (const float*)P.A, (const float*)P.inv, P.inv_stride, b, x_in,
+                                       x_zero, corr_in, ec, L.mask, cmask, x_out, corr_out, rc, omega, avg, h->stream);
+    } else {
+        launch_tile_step<float, __nv_bfloat16>(L.g, gc, mode, (const float*)P.A, (const __nv_bfloat16*)P.inv,
+                                               P.inv_stride, b, x_in, x_zero, corr_in, ec, L.mask, cmask, x_out,
+                                               corr_out, rc, omega, avg, h->stream);
+    }
+}
+
+// Pre-smoothing and restriction of a tile level: nu1 steps of Eq. (vanka)
+// from x = 0 and r_{l-1} = P^T (b - A x), in nu1 + 1 launches (the last one
+// also restricts).  The iterate alternates between the buffers x and x2 so that
+// it ends in x after the whole cycle (tile_up); returns the buffer holding it
+// after pre-smoothing.
+template <typename T>
+static T* tile_down(Hierarchy* h, int l, int prec, const T* b, T* X, int nu1, int nu2, T om, bool avg) {
+    PrecData& P = h->lev[l].p[prec];
+    const Geom& g = h->lev[l].g;
+    T* Y = (T*)P.x2;
+    T* C[2] = {(T*)P.corr, (T*)P.corr2};
+    T* bc = (T*)h->lev[l - 1].p[prec].b;
+    if (nu1 == 0) {
+        cudaMemsetAsync(X, 0, g.nodes * g.nc * sizeof(T), h->stream);
+        launch_restrict<T>(g, h->lev[l - 1].g, b, bc, h->lev[l - 1].mask, h->stream);
+        return X;
+    }
+    // materialised iterates before the final update: nu1 + nu2; the last must be in Y
+    T* out = ((nu1 + nu2) & 1) ? Y : X;
+    const T* cur = nullptr;
+    tile_launch<T>(h, l, prec, TILE_FIRST, b, nullptr, true, nullptr, nullptr, nullptr, C[0], nullptr, om, avg);
+    for (int st = 1; st < nu1; ++st) {
+        tile_launch<T>(h, l, prec, TILE_STEP, b, cur, cur == nullptr, C[(st - 1) & 1], nullptr, out, C[st & 1],
+                       nullptr, om, avg);
+        cur = out;
+        out = out == X ? Y : X;
+    }
+    tile_launch<T>(h, l, prec, TILE_RESTRICT, b, cur, cur == nullptr, C[(nu1 - 1) & 1], nullptr, out, nullptr, bc,
+                   om, avg);
+    return out;
+}
+
+// Coarse-grid correction and post-smoothing of a tile level: x = cur + P e_c,
+// nu2 steps of Eq. (vanka), the final update into X (nu2 + 1 launches).
+template <typename T>
+static void tile_up(Hierarchy* h, int l, int prec, const T* b, T* X, T* cur, int nu2, T om, bool avg) {
+    PrecData& P = h->lev[l].p[prec];
+    const Geom& g = h->lev[l].g;
+    T* Y = (T*)P.x2;
+    T* C[2] = {(T*)P.corr, (T*)P.corr2};
+    const T* ec = (const T*)h->lev[l - 1].p[prec].x;
+    if (nu2 == 0) {
+        launch_prolong_add<T>(g, h->lev[l - 1].g, ec, cur, h->lev[l].mask, h->stream);
+        if (cur != X) cudaMemcpyAsync(X, cur, g.nodes * g.nc * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+        return;
+    }
+    T* out = cur == X ? Y : X;
+    tile_launch<T>(h, l, prec, TILE_PROLONG_STEP, b, cur, false, nullptr, ec, out, C[0], nullptr, om, avg);
+    cur = out;
+    for (int st = 1; st < nu2; ++st) {
+        out = cur == X ? Y : X;
+        tile_launch<T>(h, l, prec, TILE_STEP, b, cur, false, C[(st - 1) & 1], nullptr, out, C[st & 1], nullptr, om,
+                       avg);
+        cur = out;
+    }
+    // cur is Y here (tile_down chose the parity), so the final update never reads what it writes
+    tile_launch<T>(h, l, prec, TILE_FINAL, b, cur, false, C[(nu2 - 1) & 1], nullptr, X, nullptr, nullptr, om, avg);
+}
+
 // V-cycle on levels 0..top (b_top / x_top override the top level's buffers):
-// levels above the cluster tail with one kernel per step, the tail (if any)
-// as one cluster launch, else the coarse solve.
+// levels above the cluster tail with one kernel per step (or tile-fused
+// steps), the tail (if any) as one cluster launch, else the coarse solve.
 template <typename T>
 static void vcycle_levels(Hierarchy* h, int prec, int top, int nu1, int nu2, double omega, int weighting,
                           const T* b_top, T* x_top, bool allow_tail) {
@@ -178,8 +264,13 @@ static void vcycle_levels(Hierarchy* h, int prec, int top, int nu1, int nu2, dou
     auto bptr = [&](int l) -> T* { return (l == top && b_top) ? const_cast<T*>(b_top) : (T*)h->lev[l].p[prec].b; };
     auto xptr = [&](int l) -> T* { return (l == top && x_top) ? x_top : (T*)h->lev[l].p[prec].x; };
     const int c = allow_tail ? tail_top(h, prec, top) : -1;
+    T* after_pre[kMaxLevels] = {};
     for (int l = top; l >= 1 && l > c; --l) {
         Level& L = h->lev[l];
+        if (tile_level(h, prec, l, c)) {
+            after_pre[l] = tile_down<T>(h, l, prec, bptr(l), xptr(l), nu1, nu2, om, avg);
+            continue;
+        }
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu1, true, om, avg);
         launch_spmv<T>(L.g, (const T*)L.p[prec].A, xptr(l), bptr(l), (T*)L.p[prec].r, true, s);
         launch_restrict<T>(L.g, h->lev[l - 1].g, (const T*)L.p[prec].r, bptr(l - 1), h->lev[l - 1].mask, s);
@@ -192,6 +283,10 @@ static void vcycle_levels(Hierarchy* h, int prec, int top, int nu1, int nu2, dou
     }
     for (int l = c >= 1 ? c + 1 : 1; l <= top; ++l) {
         Level& L = h->lev[l];
+        if (tile_level(h, prec, l, c)) {
+            tile_up<T>(h, l, prec, bptr(l), xptr(l), after_pre[l], nu2, om, avg);
+            continue;
+        }
         launch_prolong_add<T>(L.g, h->lev[l - 1].g, xptr(l - 1), xptr(l), L.mask, s);
         smooth_level<T>(h, l, prec, bptr(l), xptr(l), nu2, false, om, avg);
     }
@@ -307,7 +402,7 @@ static void vcycle_dispatch(Hierarchy* h, int prec, const nmg_solve_opts& o, con
 
 // Replays (capturing first if needed) the V-cycle on the level buffers as a CUDA graph.
 static nmg_status vcycle_graph(Hierarchy* h, int prec, const nmg_solve_opts& o) {
-    const int key[4] = {o.nu1, o.nu2, o.weighting, 2 * h->tail_patches[prec] + h->fused[prec]};
+    const int key[5] = {o.nu1, o.nu2, o.weighting, 2 * h->tail_patches[prec] + h->fused[prec], h->tile_patches[prec]};
     bool match = h->vgraph[prec] && std::memcmp(key, h->vgraph_key[prec], sizeof(key)) == 0 &&
                  h->vgraph_omega[prec] == o.omega;
     if (!match) {
@@ -347,7 +442,7 @@ static nmg_status validate_opts(const nmg_solve_opts* o) {
     if (!(o->rtol >= 0.0) || o->restart < 1 || o->restart > kMaxRestart || o->maxit < 0 || o->nu1 < 0 ||
         o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64 || !std::isfinite(o->omega) ||
         (o->weighting != NMG_WEIGHT_AVERAGE && o->weighting != NMG_WEIGHT_SUM) || o->use_graph < 0 || o->use_graph > 2 ||
-        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_FUSED || o->tail_patches < 0)
+        o->engine < NMG_ENGINE_AUTO || o->engine > NMG_ENGINE_FUSED || o->tail_patches < 0 || o->tile_patches < 0)
         return fail(NMG_ERR_INVALID, "invalid solve options");
     return NMG_OK;
 }
@@ -402,12 +497,14 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     const int prec = o.precision;
     if (o.engine != NMG_ENGINE_AUTO) {
         h->tail_patches[prec] = o.engine == NMG_ENGINE_PERSISTENT ? 0 : o.tail_patches;
+        h->tile_patches[prec] = o.engine == NMG_ENGINE_KERNELS ? o.tile_patches : 0;
         *engine = o.engine;
         return NMG_OK;
     }
     const int key[3] = {o.nu1, o.nu2, o.weighting};
     if (h->engine_choice[prec] && std::memcmp(key, h->engine_key[prec], sizeof(key)) == 0) {
         h->tail_patches[prec] = h->auto_tail[prec];
+        h->tile_patches[prec] = h->auto_tile[prec];
         *engine = h->engine_choice[prec];
         return NMG_OK;
     }
@@ -417,23 +514,29 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     cudaEvent_t e0, e1;
     NMG_CK(cudaEventCreate(&e0));
     NMG_CK(cudaEventCreate(&e1));
-    struct Cand { int engine, tail, fused; };
+    struct Cand { int engine, tail, fused, tile; };
     std::vector<Cand> cands;
     int last_level = -2;
     for (int tail : {0, 64, 256, 1024, 4096}) {
         h->tail_patches[prec] = tail;
         const int c = tail_top(h, prec, h->L - 1);
-        if (c != last_level)
-            for (int fz : {0, 1}) cands.push_back({fz ? NMG_ENGINE_FUSED : NMG_ENGINE_KERNELS, tail, fz});
+        if (c != last_level) {
+            for (int fz : {0, 1}) cands.push_back({fz ? NMG_ENGINE_FUSED : NMG_ENGINE_KERNELS, tail, fz, 0});
+            // tile-fused steps on the levels above the tail up to each level size (at most 16384 patches)
+            for (int l = c >= 1 ? c + 1 : 1; l < h->L; ++l)
+                if (h->lev[l].g.patches <= 16384)
+                    cands.push_back({NMG_ENGINE_KERNELS, tail, 0, (int)h->lev[l].g.patches});
+        }
         last_level = c;
     }
-    cands.push_back({NMG_ENGINE_PERSISTENT, 0, 0});
+    cands.push_back({NMG_ENGINE_PERSISTENT, 0, 0, 0});
     double best = 1e300;
     Cand pick = cands[0];
     const int64_t launches0 = g_launches;
-    h->tuning.clear();
+    h->tuning[prec].clear();
     for (const Cand& cd : cands) {
         h->tail_patches[prec] = cd.tail;
+        h->tile_patches[prec] = cd.tile;
         h->fused[prec] = cd.fused;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) ok = run_engine(h, o, cd.engine) == NMG_OK;
@@ -447,7 +550,7 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
             us = 1000.0 * ms / 5.0;
             if (us < best) { best = us; pick = cd; }
         }
-        h->tuning.push_back({cd.engine, cd.tail, cd.fused, us});
+        h->tuning[prec].push_back({cd.engine, cd.tail, cd.fused, cd.tile, us});
         cudaGetLastError();
     }
     g_launches = launches0;
@@ -462,6 +565,8 @@ static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* eng
     h->fused[prec] = pick.fused;
     h->tail_patches[prec] = pick.tail;
     h->auto_tail[prec] = pick.tail;
+    h->tile_patches[prec] = pick.tile;
+    h->auto_tile[prec] = pick.tile;
     h->engine_choice[prec] = pick.engine;
     std::memcpy(h->engine_key[prec], key, sizeof(key));
     *engine = pick.engine;
@@ -657,11 +762,13 @@ static cudaGraphExec_t cycle_graph(Hierarchy* h, const nmg_solve_opts& o, int en
     const int prec = o.precision;
     Hierarchy::LoopKey key{};
     key.nu1 = o.nu1; key.nu2 = o.nu2; key.weighting = o.weighting; key.engine = engine;
-    key.tail = h->tail_patches[prec]; key.restart = o.restart; key.maxit = o.maxit; key.gen = h->krylov_gen;
+    key.tail = h->tail_patches[prec]; key.tile = h->tile_patches[prec];
+    key.restart = o.restart; key.maxit = o.maxit; key.gen = h->krylov_gen;
     key.omega = o.omega; key.rtol = o.rtol;
     const Hierarchy::LoopKey& k0 = h->cgraph_key[prec];
     if (h->cgraph[prec] && k0.nu1 == key.nu1 && k0.nu2 == key.nu2 && k0.weighting == key.weighting &&
-        k0.engine == key.engine && k0.tail == key.tail && k0.restart == key.restart && k0.maxit == key.maxit &&
+        k0.engine == key.engine && k0.tail == key.tail && k0.tile == key.tile && k0.restart == key.restart &&
+        k0.maxit == key.maxit &&
         k0.gen == key.gen && k0.omega == key.omega && k0.rtol == key.rtol)
         return h->cgraph[prec];
     if (h->cgraph[prec]) cudaGraphExecDestroy(h->cgraph[prec]);
@@ -910,6 +1017,7 @@ nmg_status nmg_default_opts(nmg_solve_opts* o) {
     o->use_graph = 2;
     o->engine = NMG_ENGINE_AUTO;
     o->tail_patches = 0;
+    o->tile_patches = 0;
     return NMG_OK;
 }
 
@@ -988,12 +1096,14 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
             return cleanup(fail(NMG_ERR_CUDA, "mask upload failed"));
         float* A32 = nullptr;
         if (low && (st = dalloc(h, (void**)&A32, mat * sizeof(float))) != NMG_OK) return cleanup(st);
-        void* fvec[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // float work vectors shared by FP32 / BF16
+        void* fvec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // float work vectors shared by FP32 / BF16
         if (low) {
             if ((st = dalloc(h, &fvec[4], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
             for (int q = 0; q < 3; ++q)
                 if ((st = dalloc(h, &fvec[q], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
-            if (l > 0 && (st = dalloc(h, &fvec[3], (size_t)g.patches * g.np * sizeof(float))) != NMG_OK) return cleanup(st);
+            for (int q : {3, 5})
+                if (l > 0 && (st = dalloc(h, &fvec[q], (size_t)g.patches * g.np * sizeof(float))) != NMG_OK)
+                    return cleanup(st);
         }
         for (int p = 0; p < 3; ++p) {
             if (!(h->prec_mask & (1 << p))) continue;
@@ -1002,10 +1112,12 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
                 P.A = Lv.A64;
                 for (void** q : {&P.b, &P.x, &P.r, &P.x2})
                     if ((st = dalloc(h, q, nvec * sizeof(double))) != NMG_OK) return cleanup(st);
-                if (l > 0 && (st = dalloc(h, &P.corr, (size_t)g.patches * g.np * sizeof(double))) != NMG_OK) return cleanup(st);
+                for (void** q : {&P.corr, &P.corr2})
+                    if (l > 0 && (st = dalloc(h, q, (size_t)g.patches * g.np * sizeof(double))) != NMG_OK)
+                        return cleanup(st);
             } else {
                 P.A = A32;
-                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3]; P.x2 = fvec[4];
+                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3]; P.x2 = fvec[4]; P.corr2 = fvec[5];
             }
             if (l > 0) {
                 P.inv_stride = pad16((int64_t)g.np * g.np, store_size(p));
@@ -1266,17 +1378,24 @@ nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
     for (int p = 0; p < 3; ++p) {
         js += "{\"precision\": " + std::to_string(p) + ", \"engine\": " + std::to_string(h->engine_choice[p]) +
               ", \"tail_patches\": " + std::to_string(h->auto_tail[p]) +
+              ", \"tile_patches\": " + std::to_string(h->auto_tile[p]) +
               ", \"fused\": " + std::to_string(h->fused[p]) + "}";
         if (p < 2) js += ", ";
     }
-    js += "], \"last_trials\": [";
-    for (size_t i = 0; i < h->tuning.size(); ++i) {
-        char tmp[160];
-        std::snprintf(tmp, sizeof(tmp),
-                      "{\"engine\": %d, \"tail_patches\": %d, \"fused\": %d, \"us_per_vcycle\": %.3f}",
-                      h->tuning[i].engine, h->tuning[i].tail, h->tuning[i].fused, h->tuning[i].us);
-        js += tmp;
-        if (i + 1 < h->tuning.size()) js += ", ";
+    js += "], \"trials\": [";
+    for (int p = 0; p < 3; ++p) {
+        js += "[";
+        for (size_t i = 0; i < h->tuning[p].size(); ++i) {
+            const Hierarchy::Trial& t = h->tuning[p][i];
+            char tmp[160];
+            std::snprintf(tmp, sizeof(tmp),
+                          "{\"engine\": %d, \"tail_patches\": %d, \"fused\": %d, \"tile_patches\": %d, "
+                          "\"us_per_vcycle\": %.3f}",
+                          t.engine, t.tail, t.fused, t.tile, t.us);
+            js += tmp;
+            if (i + 1 < h->tuning[p].size()) js += ", ";
+        }
+        js += p < 2 ? "], " : "]";
     }
     js += "], \"device_loop\": {\"mode\": " + std::to_string(h->loop_mode) + ", \"kernels_per_step\": [" +
           std::to_string(h->cgraph_nodes[0]) + ", " + std::to_string(h->cgraph_nodes[1]) + ", " +

@@ -70,18 +70,19 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
     return (int64_t)(2 * px + ax) + (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
 }
 
-// y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
-// at a node j come from xval(j, xv) (loaded, converted or recomputed).
+// acc = (A x)_i for node i (stencil layout), summed over the stencil positions
+// in ascending order and, inside a block, over the columns; the values of x at
+// the neighbour j = i + (dx, dy, dz) come from xval(j, dx, dy, dz, xv) (loaded,
+// converted, recomputed or read from a shared-memory tile).
 template <typename T, int DIM, class XF, bool GLOBAL_A = true>
-__device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
-                                            const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
+__device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ A, XF&& xval, int64_t i,
+                                           T (&acc)[DIM + 1]) {
     constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
     int ix, iy, iz;
     node_xyz(g, i, ix, iy, iz);
     const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
-    T acc[NC];
 #pragma unroll
     for (int r = 0; r < NC; ++r) acc[r] = T(0);
 #pragma unroll
@@ -92,7 +93,7 @@ __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__
         if (ok) {
             const int64_t j = i + dx + dy * sy + dz * sz;
             T xv[NC];
-            xval(j, xv);
+            xval(j, dx, dy, dz, xv);
             const T* As = A + (int64_t)s * NB * g.ld + i;
 #pragma unroll
             for (int r = 0; r < NC; ++r)
@@ -106,6 +107,17 @@ __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__
                 }
         }
     }
+}
+
+// y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
+// at a node j come from xval(j, xv) (loaded, converted or recomputed).
+template <typename T, int DIM, class XF, bool GLOBAL_A = true>
+__device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
+                                            const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
+    constexpr int NC = DIM + 1;
+    T acc[NC];
+    auto xv4 = [&](int64_t j, int, int, int, T* xv) { xval(j, xv); };
+    spmv_acc_f<T, DIM, decltype(xv4)&, GLOBAL_A>(g, A, xv4, i, acc);
 #pragma unroll
     for (int r = 0; r < NC; ++r) y[i * NC + r] = residual ? b[i * NC + r] - acc[r] : acc[r];
 }
@@ -273,14 +285,14 @@ __device__ __forceinline__ void update_residual_node(const Geom& g, const T* __r
         b, r, true, i);
 }
 
-// (r_c)_I = (P^T r_f)_I, zero on coarse Dirichlet entries.
-template <typename T, int DIM>
-__device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, const T* __restrict__ rf,
-                                              T* __restrict__ rc, const uint8_t* __restrict__ cmask, int64_t I) {
+// sum = (P^T r_f)_I for coarse node I (Q1 full weighting), the fine values
+// coming from rval(fx, fy, fz, k) (global memory or a shared-memory tile).
+template <typename T, int DIM, class RF>
+__device__ __forceinline__ void restrict_value_f(const Geom& f, const Geom& c, RF&& rval, int64_t I,
+                                                 T (&sum)[DIM + 1]) {
     constexpr int NC = DIM + 1;
     int X, Y, Z;
     node_xyz(c, I, X, Y, Z);
-    T sum[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) sum[k] = T(0);
     const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
@@ -294,12 +306,25 @@ __device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, cons
                 const int fx = 2 * X + ox;
                 if (fx < 0 || fx >= f.nn[0]) continue;
                 const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
-                const int64_t fi = fx + (int64_t)f.nn[0] * (fy + (int64_t)f.nn[1] * fz);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) sum[k] = fma(w, rf[fi * NC + k], sum[k]);
+                for (int k = 0; k < NC; ++k) sum[k] = fma(w, rval(fx, fy, fz, k), sum[k]);
             }
         }
     }
+}
+
+// (r_c)_I = (P^T r_f)_I, zero on coarse Dirichlet entries.
+template <typename T, int DIM>
+__device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, const T* __restrict__ rf,
+                                              T* __restrict__ rc, const uint8_t* __restrict__ cmask, int64_t I) {
+    constexpr int NC = DIM + 1;
+    T sum[NC];
+    restrict_value_f<T, DIM>(
+        f, c,
+        [&](int fx, int fy, int fz, int k) {
+            return rf[(fx + (int64_t)f.nn[0] * (fy + (int64_t)f.nn[1] * fz)) * NC + k];
+        },
+        I, sum);
 #pragma unroll
     for (int k = 0; k < NC; ++k) rc[I * NC + k] = cmask[I * NC + k] ? T(0) : sum[k];
 }

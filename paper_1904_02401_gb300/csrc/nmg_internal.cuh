@@ -51,6 +51,7 @@ struct PrecData {                 // per-precision data of one level
     void* r = nullptr;
     void* corr = nullptr;         // per-patch corrections A_i^{-1} R_i d, patches * n_p
     void* x2 = nullptr;           // second iterate buffer of the fused V-cycle (ping-pong with x)
+    void* corr2 = nullptr;        // second correction buffer of the tile-fused steps (ping-pong with corr)
 };
 
 struct Level {
@@ -87,7 +88,7 @@ struct Hierarchy {
     int krylov_gen = 0;           // bumped when V / Z are reallocated
     // restart cycles as one graph with an on-device loop, per precision
     struct LoopKey {
-        int nu1, nu2, weighting, engine, tail, restart, maxit, gen;
+        int nu1, nu2, weighting, engine, tail, tile, restart, maxit, gen;
         double omega, rtol;
     };
     cudaGraphExec_t cgraph[3] = {nullptr, nullptr, nullptr};
@@ -97,7 +98,7 @@ struct Hierarchy {
     size_t bytes = 0;
     // CUDA graphs of the V-cycle, per precision (rebuilt when options change)
     cudaGraphExec_t vgraph[3] = {nullptr, nullptr, nullptr};
-    int vgraph_key[3][4] = {};    // nu1, nu2, weighting, omega bits hash
+    int vgraph_key[3][5] = {};    // nu1, nu2, weighting, tail / fused, tile threshold
     double vgraph_omega[3] = {0, 0, 0};
     // profiling of the finest-level Vanka apply
     int prof = 0;                        // 0 off, 1 events per V-cycle, 2 per finest-level Vanka apply
@@ -115,10 +116,13 @@ struct Hierarchy {
     int tail_patches[3] = {0, 0, 0};     // levels with at most this many patches run in the cluster tail
     int auto_tail[3] = {0, 0, 0};        // the autotuner's pick of tail_patches
                                          // (0: none; the autotuner may pick a threshold)
+    int tile_patches[3] = {0, 0, 0};     // levels above the tail with at most this many patches run
+                                         // tile-fused smoothing steps (tile_kernels.cu)
+    int auto_tile[3] = {0, 0, 0};        // the autotuner's pick of tile_patches
     int engine_key[3][3] = {};
     double engine_us[3][2] = {};
-    struct Trial { int engine, tail, fused; double us; };
-    std::vector<Trial> tuning;             // the autotuner's last measurements
+    struct Trial { int engine, tail, fused, tile; double us; };
+    std::vector<Trial> tuning[3];          // the autotuner's measurements, per precision
     double prof_bytes = 0.0;
     std::vector<void*> allocs;
 };
@@ -181,6 +185,23 @@ template <typename T>
 void launch_coarse_gemv(const double* inv, int64_t n, const T* b, T* x, cudaStream_t s);
 template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tile-fused smoothing steps (tile_kernels.cu): one CTA per tile of patches
+// recomputes the previous update on its node region, the defect on its patch
+// nodes, and then solves its patches (or restricts the residual).
+// ---------------------------------------------------------------------------
+enum TileMode {
+    TILE_FIRST = 0,          // x = 0: d = b; corr_out = patch solves
+    TILE_STEP = 1,           // x = x_in + w corr_in (x_out, owned nodes); d = b - A x; corr_out
+    TILE_PROLONG_STEP = 2,   // x = x_in + P ec (x_out, owned nodes); d = b - A x; corr_out
+    TILE_RESTRICT = 3,       // x = x_in + w corr_in (x_out, owned nodes); rc = P^T (b - A x)
+    TILE_FINAL = 4           // x_out = x_in + w corr_in on every node
+};
+template <typename T, typename TS>
+void launch_tile_step(const Geom& g, const Geom& gc, int mode, const T* A, const TS* inv, int64_t inv_stride,
+                      const T* b, const T* x_in, bool x_zero, const T* corr_in, const T* ec, const uint8_t* fmask,
+                      const uint8_t* cmask, T* x_out, T* corr_out, T* rc, T omega, bool average, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Launchers (krylov_kernels.cu): FP64 outer FGMRES

@@ -66,6 +66,7 @@ class nmg_solve_opts(C.Structure):
         ("use_graph", C.c_int),
         ("engine", C.c_int),
         ("tail_patches", C.c_int),
+        ("tile_patches", C.c_int),
     ]
 
 

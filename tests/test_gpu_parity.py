@@ -363,8 +363,42 @@ def test_engines_agree(nmg, built, sessions, case, prec):
         o = solve_opts(precision=prec, use_graph=graph, engine=engine, tail_patches=tail)
         nmg.check(nmg.nmg_vcycle(S.handle, o, r, z))
         outs.append(z)
+    # tile-fused steps: on level 1 only, on every level (finest included), above a cluster tail
+    for graph, tail, tile in ((0, 0, p1), (0, 0, 1 << 30), (1, 0, 1 << 30), (1, p1, 1 << 30)):
+        z = torch.zeros_like(r)
+        o = solve_opts(precision=prec, use_graph=graph, engine=nmg.NMG_ENGINE_KERNELS, tail_patches=tail,
+                       tile_patches=tile)
+        nmg.check(nmg.nmg_vcycle(S.handle, o, r, z))
+        outs.append(z)
     for k in range(1, len(outs)):
         assert torch.equal(outs[0], outs[k]), k
+
+
+@pytest.mark.parametrize("case", ["2d_24x40_3lev", "3d_8x12x16_3lev"])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nu", [(1, 1), (1, 3), (3, 1), (0, 2), (2, 0), (0, 0)])
+@pytest.mark.parametrize("weighting", [0, 1])
+def test_tile_steps_agree(nmg, built, sessions, case, prec, nu, weighting):
+    """Tile-fused smoothing steps (one launch per Vanka step on a tile level,
+    the pre-smoothing's last step also restricting) give the V-cycle of the
+    one-kernel-per-pass path bit for bit, for any numbers of pre- and
+    post-smoothing steps (the iterate's buffer parity, the zero first iterate
+    and the skipped steps), both weightings of Eq. (vanka), on ragged tiles."""
+    from paper_1904_02401_gb300.session import solve_opts
+    s, h = built[case]
+    S = sessions[case]
+    dt = vdtype(prec)
+    r = cu(s.rhs.astype(dt), dt)
+    om = 0.8 if weighting == nmg.NMG_WEIGHT_AVERAGE else 0.3
+    outs = []
+    for tile in (0, 1 << 30):
+        z = torch.zeros_like(r)
+        o = solve_opts(precision=prec, use_graph=0, engine=nmg.NMG_ENGINE_KERNELS, nu1=nu[0], nu2=nu[1],
+                       weighting=weighting, omega=om, tile_patches=tile)
+        nmg.check(nmg.nmg_vcycle(S.handle, o, r, z))
+        outs.append(z)
+    assert torch.equal(outs[0], outs[1])
+    assert torch.isfinite(outs[0]).all()
 
 
 @pytest.mark.parametrize("case", list(CASES))
