@@ -307,6 +307,7 @@ def gpu_arm(args):
     # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
     ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
     _, _, vprof = timed_solves(args.precision, args.steps, min(use_graph, 1), profile=1)
+    _, _, sprof = timed_solves(args.precision, args.steps, 0, profile=3, engine=nmg.NMG_ENGINE_KERNELS)
     rep = C.create_string_buffer(32768)
     nmg.check(nmg.nmg_autotune_report(S.handle, rep, 32768))
     # plain FP64 path on the same mesh
@@ -374,6 +375,7 @@ def gpu_arm(args):
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
                      "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
+        "spmv": _spmv_line(sprof, hbm, args.steps),
         "vcycle": {"ms": vms / vcount if vcount else None, "bytes": vbytes,
                    "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
                    "engine": {1: "per-step kernels", 2: "persistent kernel",
@@ -398,6 +400,19 @@ def gpu_arm(args):
     S.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _spmv_line(prof, hbm, steps):
+    """The finest-level residual product (block SpMV), timed per launch with
+    events on its stream inside plain-launch solves: algorithmic bytes (Q1
+    blocks once, x, b and r once) over the mean launch time."""
+    ms, cnt, nbytes = prof
+    if not cnt:
+        return None
+    gbs = nbytes / (ms / cnt * 1e-3) / 1e9
+    return {"kernel": "k_spmv / k_spmv_rows (finest-level residual product)", "bound": "hbm", "achieved": gbs,
+            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "launch_ms": ms / cnt, "bytes_per_launch": nbytes,
+            "timed": f"{cnt} launches over {steps} solves (events around each launch)"}
 
 
 def _matvec(sysm, x):

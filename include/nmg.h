@@ -241,8 +241,9 @@ nmg_status nmg_destroy_hierarchy(nmg_hierarchy* h);
 
 /* ---- kernel timing on the hierarchy's stream.  mode 1: every V-cycle of
  * later solves is bracketed by CUDA events; mode 2: every finest-level Vanka
- * apply launch is (plain launches only: use_graph = 0, engine KERNELS);
- * mode 0: off. */
+ * apply launch is; mode 3: every finest-level residual product (block SpMV)
+ * launch is (modes 2 and 3: plain launches only, use_graph = 0, engine
+ * KERNELS); mode 0: off. */
 nmg_status nmg_profile_enable(nmg_hierarchy* h, int mode);
 /* Total milliseconds and count of the timed V-cycles / launches since enabling,
  * and the algorithmic bytes one of them moves (every patch inverse, matrix and

@@ -129,12 +129,27 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         h->prof_bytes = (double)g.patches * g.np * g.np * si + (double)g.nodes * g.nc * sv +
                         (double)g.patches * g.np * sv;
     }
+    // mode 3: the residual products of the finest level; algorithmic bytes = the
+    // Q1 blocks of the matrix once, x, b and r once
+    const bool sprof = h->prof == 3 && l == h->L - 1;
+    if (sprof) {
+        const double sv = (double)sizeof(T);
+        double nnzb = 1.0;
+        for (int k = 0; k < g.dim; ++k) nnzb *= 3.0 * g.nn[k] - 2.0;
+        h->prof_bytes = nnzb * g.nc * g.nc * sv + 3.0 * (double)g.nodes * g.nc * sv;
+    }
     for (int st = 0; st < steps; ++st) {
         const T* d;
         if (st == 0 && x_zero) {
             d = b;
         } else {
+            const bool srec = sprof && h->prof_used < (int)h->prof_ev.size() / 2;
+            if (srec) cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
             launch_spmv<T>(g, (const T*)P.A, x, b, (T*)P.r, true, s);
+            if (srec) {
+                cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
+                h->prof_used++;
+            }
             d = (const T*)P.r;
         }
         const bool rec = prof && h->prof_used < (int)h->prof_ev.size() / 2;
@@ -723,11 +738,13 @@ static void job_enqueue_cycle(SolveJob& J) {
 
 // One FGMRES step j (read on the device from cyc[0]): z_j = M^{-1} v_j (v_j is
 // already the V-cycle's right-hand side, written by the scaling that produced
-// it), w = A z_j in FP64 with z_j stored as basis vector Z_j, two classical
-// Gram-Schmidt passes (the second ends with ||w|| and the Givens update),
-// v_{j+1} = w / h_{j+1,j}, and the on-device decision whether the cycle goes
-// on.  in_loop: the launches are being captured as the body of a graph loop
-// whose condition the decision sets (the V-cycle is captured inline then).
+// it); w = A z_j in FP64 with z_j stored as basis vector Z_j, fused with the
+// first classical Gram-Schmidt pass; the first update fused with the second
+// pass, ||w|| and the Givens update; the second update fused with the
+// scaling v_{j+1} = w / h_{j+1,j}; and the on-device decision whether the
+// cycle goes on.  in_loop: the launches are being captured as the body of a
+// graph loop whose condition the decision sets (the V-cycle is captured
+// inline then).
 static nmg_status enqueue_step(Hierarchy* h, const nmg_solve_opts& o, int engine, bool in_loop,
                                cudaGraphConditionalHandle loop) {
     const Geom& g = h->lev[h->L - 1].g;
@@ -742,12 +759,18 @@ static nmg_status enqueue_step(Hierarchy* h, const nmg_solve_opts& o, int engine
     }
     const PrecData& PF = h->lev[h->L - 1].p[o.precision];
     double* A64 = h->lev[h->L - 1].A64;
-    if (o.precision == NMG_PREC_FP64) launch_spmv_zstore<double>(g, A64, (const double*)PF.x, h->Z, n, h->cyc, h->w64, s);
-    else launch_spmv_zstore<float>(g, A64, (const float*)PF.x, h->Z, n, h->cyc, h->w64, s);
-    launch_multidot_fused(h->V, n, h->cyc, h->w64, n, h->partial, h->scal + S_HC, h->counters, s);
-    launch_gs_update_dot(h->V, n, h->cyc, h->scal + S_HC, h->w64, n, h->partial, h->scal + S_Y, h->counters, s);
-    launch_gs_norm_arnoldi(h->V, n, h->scal + S_Y, h->w64, n, h->partial, h->scal, h->cyc, m, h->counters, s);
-    scale_into_vcycle_input(h, o, h->w64, true);
+    if (o.precision == NMG_PREC_FP64)
+        launch_spmv_zstore_dots<double>(g, A64, (const double*)PF.x, h->Z, h->w64, h->V, n, h->cyc, h->partial,
+                                        h->scal + S_HC, h->counters, s);
+    else
+        launch_spmv_zstore_dots<float>(g, A64, (const float*)PF.x, h->Z, h->w64, h->V, n, h->cyc, h->partial,
+                                       h->scal + S_HC, h->counters, s);
+    launch_gs_update_dot_norm(h->V, n, h->cyc, h->w64, n, h->partial, h->scal, m, h->counters, s);
+    Level& F = h->lev[h->L - 1];
+    if (o.precision == NMG_PREC_FP64)
+        launch_gs_update_scale<double>(h->V, n, h->cyc, h->scal, h->w64, (double*)F.p[NMG_PREC_FP64].b, n, s);
+    else
+        launch_gs_update_scale<float>(h->V, n, h->cyc, h->scal, h->w64, (float*)F.p[o.precision].b, n, s);
     launch_decide(h->scal, h->cyc, o.rtol, o.maxit, m, loop, in_loop, s);
     return NMG_OK;
 }
@@ -1363,7 +1386,7 @@ nmg_status nmg_profile_enable(nmg_hierarchy* h, int enable) {
         for (auto& e : h->prof_ev)
             if (cudaEventCreate(&e) != cudaSuccess) return fail(NMG_ERR_CUDA, "event creation failed");
     }
-    if (enable < 0 || enable > 2) return fail(NMG_ERR_INVALID, "profile mode must be 0, 1 or 2");
+    if (enable < 0 || enable > 3) return fail(NMG_ERR_INVALID, "profile mode must be 0, 1, 2 or 3");
     h->prof = enable;
     h->prof_used = 0;
     h->prof_ms = 0.0;

@@ -1,10 +1,11 @@
-// FP64 kernels of the outer flexible GMRES (Section 4.3 item (I)): classical
-// Gram-Schmidt with re-orthogonalisation (a multi-dot, a fused multi-axpy +
-// multi-dot, a multi-axpy + norm), the Givens update of the Hessenberg column,
-// the on-device step decision and the final x += Z y.  All reductions use a
-// fixed grid and a fixed summation tree, so results are bitwise reproducible
-// run to run.
-#include "nmg_internal.cuh"
+// FP64 kernels of the outer flexible GMRES (Section 4.3 item (I)): the outer
+// product w = A z_j fused with the first classical Gram-Schmidt pass, the
+// second pass fused with the first update and the norm, the Givens update of
+// the Hessenberg column, the second update fused with the scaling into the
+// next basis vector, the on-device step decision and the final x += Z y.  All
+// reductions use a fixed grid, a fixed split of the vectors between blocks
+// and a fixed summation tree, so results are bitwise reproducible run to run.
+#include "elem.cuh"
 
 namespace nmg {
 
@@ -188,11 +189,23 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // spend few FP64 additions: a thread accumulates up to 32 dot products, a warp
 // reduces its 32 values by a transposing butterfly (31 additions per lane
 // instead of 5 per value), the block adds its warps, and the last block sums
-// the block partials in a fixed order.  Results are bitwise reproducible run
-// to run.
+// the block partials in a fixed order.  Every block owns one contiguous,
+// equal share of the vector (block_range), so the SMs finish together.
+// Results are bitwise reproducible run to run.
 constexpr int kMdThreads = 256;
 constexpr int kMdWarps = kMdThreads / 32;
 constexpr int kMdChunk = 32;   // vectors per pass over w
+// row of the partial-sum buffer (rows of kDotBlocks doubles) holding the
+// block sums of ||w||^2, after the two chunks of multi-dot partials
+constexpr int kNormRow = 2 * kMdChunk;
+static_assert((kMaxRestart + kMdChunk - 1) / kMdChunk <= 2 && kNormRow < kMaxRestart + 2,
+              "two chunks of partials, then the norm row, inside the partial buffer");
+
+// [lo, hi) = this block's share of n items (launched on kDotBlocks blocks).
+__device__ __forceinline__ void block_range(int64_t n, int64_t& lo, int64_t& hi) {
+    lo = n * blockIdx.x / gridDim.x;
+    hi = n * (blockIdx.x + 1) / gridDim.x;
+}
 
 // Warp reduction of W per-lane values (W a power of two <= 32): a
 // transposing butterfly over the offsets W/2 .. 1 (W - 1 additions per lane)
@@ -234,19 +247,20 @@ __device__ __forceinline__ void block_partials(double (&acc)[W], double* __restr
     __syncthreads();
 }
 
-// acc[k] = sum over this thread's elements of V_{c0+k} . w for k < W (columns
-// at or beyond c0 + nv contribute zeros: they are not read).
+// acc[k] = sum over this thread's elements i = lo + t, lo + t + 256, ... < hi
+// of V_{c0+k}[i] w[i] for k < W (columns at or beyond c0 + nv contribute
+// zeros: they are not read).  w may have been written earlier in the same
+// kernel (by this block), so it is read through the L2 (ld.global.cg).
 template <int W>
-__device__ __forceinline__ void dots(const double* __restrict__ V, int64_t ldv, int c0, int nv,
-                                     const double* __restrict__ w, int64_t n, double (&acc)[W]) {
-    const int64_t T = (int64_t)gridDim.x * kMdThreads;
+__device__ __forceinline__ void dots(const double* __restrict__ V, int64_t ldv, int c0, int nv, const double* w,
+                                     int64_t lo, int64_t hi, double (&acc)[W]) {
 #pragma unroll
     for (int k = 0; k < W; ++k) acc[k] = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
-        const double wi = w[i];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kMdThreads) {
+        const double wi = __ldcg(w + i);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const double v = k < nv ? V[(int64_t)(c0 + k) * ldv + i] : 0.0;
+            const double v = k < nv ? __ldg(V + (int64_t)(c0 + k) * ldv + i) : 0.0;
             acc[k] = fma(v, wi, acc[k]);
         }
     }
@@ -254,13 +268,13 @@ __device__ __forceinline__ void dots(const double* __restrict__ V, int64_t ldv, 
 
 // One chunk of at most 32 dot products, with the accumulator width the
 // smallest power of two >= nv (FP64 work not spent on absent vectors).
-__device__ __forceinline__ void dots_chunk(const double* __restrict__ V, int64_t ldv, int c0, int nv,
-                                           const double* __restrict__ w, int64_t n, double* __restrict__ partial,
-                                           int chunk, int lane, int warp) {
+__device__ __forceinline__ void dots_chunk(const double* __restrict__ V, int64_t ldv, int c0, int nv, const double* w,
+                                           int64_t lo, int64_t hi, double* __restrict__ partial, int chunk, int lane,
+                                           int warp) {
 #define NMG_DOTS(W)                                        \
     {                                                      \
         double acc[W];                                     \
-        dots<W>(V, ldv, c0, nv, w, n, acc);                \
+        dots<W>(V, ldv, c0, nv, w, lo, hi, acc);           \
         block_partials<W>(acc, partial, chunk, lane, warp); \
     }
     if (nv > 16) NMG_DOTS(32)
@@ -270,6 +284,13 @@ __device__ __forceinline__ void dots_chunk(const double* __restrict__ V, int64_t
     else if (nv > 1) NMG_DOTS(2)
     else NMG_DOTS(1)
 #undef NMG_DOTS
+}
+
+// The nvec dot products of the current Arnoldi step for this block's share.
+__device__ __forceinline__ void dots_all(const double* __restrict__ V, int64_t ldv, int nvec, const double* w,
+                                         int64_t lo, int64_t hi, double* __restrict__ partial, int lane, int warp) {
+    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk)
+        dots_chunk(V, ldv, c0, min(kMdChunk, nvec - c0), w, lo, hi, partial, chunk, lane, warp);
 }
 
 // In the last block: out[k] = sum over the blocks of the partials of value k
@@ -302,79 +323,117 @@ __device__ void finish_chunks(const double* __restrict__ partial, int nvec, doub
     }
 }
 
-// out[k] = V_k . w for the nvec = cyc[0] + 1 vectors of the current Arnoldi
-// step (first Gram-Schmidt pass), in one launch.
+// Outer product of step j = cyc[0] fused with the first Gram-Schmidt pass:
+// Z_j = z (the V-cycle output xf, widened exactly to FP64), w = A z in FP64,
+// and out[k] = V_k . w for k <= j.  Each block first computes w on its share
+// of the nodes, then the dot products over the same unknowns.
+template <typename TX, int DIM>
 __global__ void __launch_bounds__(kMdThreads)
-k_multidot_fused(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ w,
-                 int64_t n, double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
+k_spmv_zstore_dots(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ Z,
+                   double* w, const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc,
+                   double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
     NMG_PDL_ENTRY();
-    const int nvec = cyc[0] + 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk)
-        dots_chunk(V, ldv, c0, min(kMdChunk, nvec - c0), w, n, partial, chunk, lane, warp);
-    if (!last_block(counter)) return;
-    finish_chunks(partial, nvec, out, lane, warp);
-}
-
-// Second Gram-Schmidt pass fused with the first update: w <- w - sum_k h_k V_k
-// (h = the first pass's coefficients) and out[k] = V_k . w_new, reading V
-// once for both.
-__global__ void __launch_bounds__(kMdThreads)
-k_gs_update_dot(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ h,
-                double* __restrict__ w, int64_t n, double* __restrict__ partial, double* __restrict__ out,
-                unsigned* counter) {
-    NMG_PDL_ENTRY();
-    __shared__ double hs[kMaxRestart + 1];
-    const int nvec = cyc[0] + 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < nvec; k += kMdThreads) hs[k] = h[k];
-    __syncthreads();
-    const int64_t T = (int64_t)gridDim.x * kMdThreads;
-    for (int64_t i = blockIdx.x * (int64_t)kMdThreads + threadIdx.x; i < n; i += T) {
-        double v = w[i];
-#pragma unroll 8
-        for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
-        w[i] = v;
-    }
-    // this thread reads back only the elements it wrote
-    for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk)
-        dots_chunk(V, ldv, c0, min(kMdChunk, nvec - c0), w, n, partial, chunk, lane, warp);
-    if (!last_block(counter)) return;
-    finish_chunks(partial, nvec, out, lane, warp);
-}
-
-// Second Gram-Schmidt pass w -= sum h_k V_k, ||w|| into scal[S_HC + j + 1], then
-// the Givens update of Hessenberg column j = cyc[0], in one launch.
-__global__ void __launch_bounds__(kThreads)
-k_gs_norm_arnoldi(const double* __restrict__ V, int64_t ldv, const double* __restrict__ h, double* __restrict__ w,
-                  int64_t n, double* __restrict__ partial, double* scal, const int* cyc, int m, unsigned* counter) {
-    NMG_PDL_ENTRY();
-    __shared__ double red[kThreads / 32];
-    __shared__ double hs[kMaxRestart + 1];
+    constexpr int NC = DIM + 1;
     const int j = cyc[0], nvec = j + 1;
-    for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* z64 = Z + (int64_t)j * ldv;
+    int64_t lo, hi;
+    block_range(g.nodes, lo, hi);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kMdThreads) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) z64[i * NC + c] = elem::widen<double, TX>(xf[i * NC + c]);
+        double acc[NC];
+        elem::spmv_acc_f<double, DIM>(
+            g, A,
+            [&](int64_t jn, int, int, int, double* xv) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) xv[c] = elem::widen<double, TX>(xf[jn * NC + c]);
+            },
+            i, acc);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[i * NC + c] = acc[c];
+    }
+    __syncthreads();   // the block's w is complete
+    dots_all(V, ldv, nvec, w, lo * NC, hi * NC, partial, lane, warp);
+    if (!last_block(counter)) return;
+    finish_chunks(partial, nvec, out, lane, warp);
+}
+
+// Second Gram-Schmidt pass fused with the first update and the norm:
+// w <- w - sum_k h1_k V_k (h1 = scal[S_HC..], the first pass), ||w||^2 and
+// h2_k = V_k . w (into scal[S_Y..]); then, in the last block,
+// h_{j+1,j} = ||w - V h2|| = sqrt(||w||^2 - ||h2||^2) (Pythagoras: the V_k
+// are orthonormal, as in low-synchronisation CGS2) and the Givens update of
+// column j.  Each thread reads back only the elements it wrote.
+__global__ void __launch_bounds__(kMdThreads)
+k_gs_update_dot_norm(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, double* w, int64_t n,
+                     double* __restrict__ partial, double* scal, int m, unsigned* counter) {
+    NMG_PDL_ENTRY();
+    __shared__ double hs[kMaxRestart + 1];
+    __shared__ double red[kMdWarps];
+    __shared__ double s_hnext;
+    const int j = cyc[0], nvec = j + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < nvec; k += kMdThreads) hs[k] = scal[S_HC + k];
     __syncthreads();
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kThreads) {
+    int64_t lo, hi;
+    block_range(n, lo, hi);
+    double ww = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kMdThreads) {
         double v = w[i];
 #pragma unroll 8
         for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
         w[i] = v;
-        acc = fma(v, v, acc);
+        ww = fma(v, v, ww);
     }
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    for (int off = 16; off > 0; off >>= 1) ww += __shfl_down_sync(0xffffffffu, ww, off);
+    if (lane == 0) red[warp] = ww;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = red[0];
+#pragma unroll
+        for (int k = 1; k < kMdWarps; ++k) t += red[k];
+        partial[(int64_t)kNormRow * kDotBlocks + blockIdx.x] = t;
+    }
+    dots_all(V, ldv, nvec, w, lo, hi, partial, lane, warp);
     if (!last_block(counter)) return;
-    __shared__ double s_hnext;
-    if (threadIdx.x < 32) {
-        const double t = finish_row(partial, 0, threadIdx.x);
-        if (threadIdx.x == 0) {
-            s_hnext = sqrt(t);
+    finish_chunks(partial, nvec, scal + S_Y, lane, warp);
+    if (warp == 0) {
+        const double t = finish_row(partial, kNormRow, lane);
+        if (lane == 0) {
+            double hh = 0.0;
+            for (int k = 0; k < nvec; ++k) hh = fma(scal[S_Y + k], scal[S_Y + k], hh);
+            const double d = t - hh;
+            s_hnext = d > 0.0 ? sqrt(d) : 0.0;
             scal[S_HC + j + 1] = s_hnext;
         }
     }
     __syncthreads();
     arnoldi_column(scal, j, m, s_hnext);
+}
+
+// Second update fused with the scaling: v_{j+1} = (w - sum_k h2_k V_k) *
+// scal[S_INVH] into basis column j + 1 and, converted, into vin (the
+// right-hand side of the next V-cycle).
+template <typename TV>
+__global__ void __launch_bounds__(kThreads)
+k_gs_update_scale(double* V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ scal,
+                  const double* __restrict__ w, TV* __restrict__ vin, int64_t n) {
+    NMG_PDL_ENTRY();
+    __shared__ double hs[kMaxRestart + 1];
+    const int j = cyc[0], nvec = j + 1;
+    for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = scal[S_Y + k];
+    __syncthreads();
+    const double a = scal[S_INVH];
+    double* y = V + (int64_t)(j + 1) * ldv;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        double v = w[i];
+#pragma unroll 8
+        for (int k = 0; k < nvec; ++k) v = fma(-hs[k], V[(int64_t)k * ldv + i], v);
+        const double sv = a * v;
+        y[i] = sv;
+        vin[i] = (TV)sv;
+    }
 }
 
 // v = x * scal[S_INVH] into the Krylov basis (column cyc[0] + 1 when next,
@@ -435,24 +494,42 @@ void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ld
 
 namespace nmg {
 
-void launch_multidot_fused(const double* V, int64_t ldv, const int* cyc, const double* w, int64_t n, double* partial,
-                           double* out, unsigned* counter, cudaStream_t s) {
+template <typename TX>
+void launch_spmv_zstore_dots(const Geom& g, const double* A, const TX* xf, double* Z, double* w, const double* V,
+                             int64_t ldv, const int* cyc, double* partial, double* out, unsigned* counter,
+                             cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_multidot_fused, dim3(kDotBlocks), dim3(kMdThreads), 0, s, V, ldv, cyc, w, n, partial, out, counter);
+    if (g.dim == 2)
+        pdl_launch(k_spmv_zstore_dots<TX, 2>, dim3(kDotBlocks), dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc,
+                   partial, out, counter);
+    else
+        pdl_launch(k_spmv_zstore_dots<TX, 3>, dim3(kDotBlocks), dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc,
+                   partial, out, counter);
 }
+template void launch_spmv_zstore_dots<float>(const Geom&, const double*, const float*, double*, double*,
+                                             const double*, int64_t, const int*, double*, double*, unsigned*,
+                                             cudaStream_t);
+template void launch_spmv_zstore_dots<double>(const Geom&, const double*, const double*, double*, double*,
+                                              const double*, int64_t, const int*, double*, double*, unsigned*,
+                                              cudaStream_t);
 
-void launch_gs_update_dot(const double* V, int64_t ldv, const int* cyc, const double* h, double* w, int64_t n,
-                          double* partial, double* out, unsigned* counter, cudaStream_t s) {
+void launch_gs_update_dot_norm(const double* V, int64_t ldv, const int* cyc, double* w, int64_t n, double* partial,
+                               double* scal, int m, unsigned* counter, cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_gs_update_dot, dim3(kDotBlocks), dim3(kMdThreads), 0, s, V, ldv, cyc, h, w, n, partial, out, counter);
-}
-
-void launch_gs_norm_arnoldi(const double* V, int64_t ldv, const double* h, double* w, int64_t n, double* partial,
-                            double* scal, const int* cyc, int m, unsigned* counter, cudaStream_t s) {
-    g_launches += 1;
-    pdl_launch(k_gs_norm_arnoldi, dim3(kDotBlocks), dim3(kThreads), 0, s, V, ldv, h, w, n, partial, scal, cyc, m,
+    pdl_launch(k_gs_update_dot_norm, dim3(kDotBlocks), dim3(kMdThreads), 0, s, V, ldv, cyc, w, n, partial, scal, m,
                counter);
 }
+
+template <typename TV>
+void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, const double* scal, const double* w, TV* vin,
+                            int64_t n, cudaStream_t s) {
+    g_launches += 1;
+    pdl_launch(k_gs_update_scale<TV>, dim3(grid_for(n)), dim3(kThreads), 0, s, V, ldv, cyc, scal, w, vin, n);
+}
+template void launch_gs_update_scale<float>(double*, int64_t, const int*, const double*, const double*, float*,
+                                            int64_t, cudaStream_t);
+template void launch_gs_update_scale<double>(double*, int64_t, const int*, const double*, const double*, double*,
+                                             int64_t, cudaStream_t);
 
 template <typename TV>
 void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,

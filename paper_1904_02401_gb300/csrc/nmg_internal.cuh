@@ -225,20 +225,23 @@ void launch_norm2(const double* x, int64_t n, double* partial, double* out, cuda
 void launch_start_cycle(double* scal, int m, int* cyc, cudaStream_t s);
 void launch_solve_update(double* scal, int k, int m, const double* Z, int64_t ldz, double* x,
                          int64_t n, cudaStream_t s);
-void launch_multidot_fused(const double* V, int64_t ldv, const int* cyc, const double* w, int64_t n, double* partial,
-                           double* out, unsigned* counter, cudaStream_t s);
-void launch_gs_update_dot(const double* V, int64_t ldv, const int* cyc, const double* h, double* w, int64_t n,
-                          double* partial, double* out, unsigned* counter, cudaStream_t s);
-void launch_gs_norm_arnoldi(const double* V, int64_t ldv, const double* h, double* w, int64_t n, double* partial,
-                            double* scal, const int* cyc, int m, unsigned* counter, cudaStream_t s);
+// Step j = cyc[0]: Z_j = widened xf, w = A Z_j (FP64) and out = V_{0..j}^T w.
+template <typename TX>
+void launch_spmv_zstore_dots(const Geom& g, const double* A, const TX* xf, double* Z, double* w, const double* V,
+                             int64_t ldv, const int* cyc, double* partial, double* out, unsigned* counter,
+                             cudaStream_t s);
+// w -= V scal[S_HC..]; scal[S_Y..] = V^T w; h_{j+1,j} and the Givens update of column j.
+void launch_gs_update_dot_norm(const double* V, int64_t ldv, const int* cyc, double* w, int64_t n, double* partial,
+                               double* scal, int m, unsigned* counter, cudaStream_t s);
+// V_{j+1} = (w - V scal[S_Y..]) * scal[S_INVH], also converted into vin.
+template <typename TV>
+void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, const double* scal, const double* w, TV* vin,
+                            int64_t n, cudaStream_t s);
 template <typename TV>
 void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,
                           TV* vin, int64_t n, cudaStream_t s);
 void launch_decide(const double* scal, int* cyc, double rtol, int maxit, int m, cudaGraphConditionalHandle loop,
                    bool in_loop, cudaStream_t s);
-template <typename TX>
-void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* Z, int64_t ldz, const int* cyc, double* w,
-                        cudaStream_t s);
 
 }  // namespace nmg
 

@@ -46,23 +46,6 @@ k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* _
     spmv_row<T, DIM>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
 }
 
-// w = A z in FP64 with z read from the V-cycle output xf (stored as TX) and
-// written, converted, to Z_j (the FGMRES basis vector of step j = cyc[0]):
-// the outer product of one FGMRES iteration without a separate conversion pass.
-template <typename TX, int DIM>
-__global__ void __launch_bounds__(256, 1)
-k_spmv_zstore(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ Z, int64_t ldz,
-              const int* __restrict__ cyc, double* __restrict__ w) {
-    NMG_PDL_ENTRY();
-    constexpr int NC = DIM + 1;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= g.nodes) return;
-    double* z64 = Z + (int64_t)cyc[0] * ldz;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) z64[i * NC + c] = widen<double, TX>(xf[i * NC + c]);
-    spmv_node<double, DIM, TX>(g, A, xf, nullptr, w, false, i);
-}
-
 // corr_i = A_i^{-1} R_i d for every patch i: one warp per patch.  The patch
 // inverse is column-major, so for each column j the 32 lanes read 32
 // consecutive entries (one coalesced 128-byte segment in FP32) and multiply
@@ -277,19 +260,6 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
     else
         pdl_launch(k_spmv<T, 2>, dim3(blocks_for(g.nodes, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
 }
-
-template <typename TX>
-void launch_spmv_zstore(const Geom& g, const double* A, const TX* xf, double* Z, int64_t ldz, const int* cyc, double* w,
-                        cudaStream_t s) {
-    g_launches += 1;
-    const dim3 grid(blocks_for(g.nodes, 256));
-    if (g.dim == 2) pdl_launch(k_spmv_zstore<TX, 2>, grid, dim3(256), 0, s, g, A, xf, Z, ldz, cyc, w);
-    else pdl_launch(k_spmv_zstore<TX, 3>, grid, dim3(256), 0, s, g, A, xf, Z, ldz, cyc, w);
-}
-template void launch_spmv_zstore<float>(const Geom&, const double*, const float*, double*, int64_t, const int*,
-                                        double*, cudaStream_t);
-template void launch_spmv_zstore<double>(const Geom&, const double*, const double*, double*, int64_t, const int*,
-                                         double*, cudaStream_t);
 
 // Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
 // resident count comes from the occupancy calculator for the kernel's shared
