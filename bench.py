@@ -60,6 +60,8 @@ def parse():
                     help="1: V-cycle graphs with host-stepped FGMRES; 2: also one on-device loop per restart cycle")
     ap.add_argument("--engine", default="auto", choices=["auto", "kernels", "persistent", "fused"],
                     help="V-cycle engine (auto: the autotuner picks it on the first solve)")
+    ap.add_argument("--tile-patches", type=int, default=0,
+                    help="engine kernels: levels with at most this many patches run tile-fused Vanka steps")
     ap.add_argument("--tail-patches", type=int, default=0,
                     help="with --engine kernels/fused: levels with at most this many patches run in the cluster tail")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
@@ -260,7 +262,8 @@ def gpu_arm(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine, tail_patches=args.tail_patches)
+                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine, tail_patches=args.tail_patches,
+                                tile_patches=args.tile_patches)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -281,7 +284,7 @@ def gpu_arm(args):
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
             info = S.solve(b, x, precision=args.precision, use_graph=use_graph, engine=engine,
-                           tail_patches=args.tail_patches)
+                           tail_patches=args.tail_patches, tile_patches=args.tile_patches)
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
         if rank == 0:
@@ -432,6 +435,9 @@ def serving_arm(args):
     hierarchy from numpy default_rng(2) and its right-hand side from the CUDA
     generator seeded 11 + 2 i.  Arrivals are a Poisson stream (seed 2) at 80%
     of the saturated throughput measured first on a burst of the same mix.
+    One server (16 slots, 150 GB) serves the warm-up, the burst and the timed
+    stream, so the workspaces it adds for concurrent requests on one
+    hierarchy are made during the warm-up.
     """
     import ctypes as C
 
@@ -477,9 +483,10 @@ def serving_arm(args):
         torch.cuda.synchronize()
         return out
 
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(budget, 16, server))
+
     def run(reqs, rate):
-        server = C.c_void_p()
-        nmg.check(nmg.nmg_server_create(budget, 16, server))
         tickets = []
         start = time.perf_counter()
         arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
@@ -498,7 +505,6 @@ def serving_arm(args):
             lat.append(info.ms_total)
             its.append(info.iterations)
         wall = time.perf_counter() - start
-        nmg.nmg_server_destroy(server)
         return wall, lat, its, bad
 
     burst = make_requests(200, 1_000_011)
@@ -509,6 +515,7 @@ def serving_arm(args):
     reqs = make_requests(args.requests, 11)
     rate = 0.8 * saturated
     wall, lat, its, bad = run(reqs, rate)
+    nmg.nmg_server_destroy(server)
     lat_sorted = sorted(lat)
     line = {
         "metric": METRIC, "value": statistics.median(lat), "unit": "ms (p50 submit-to-completion latency)",

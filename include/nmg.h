@@ -169,9 +169,10 @@ nmg_status nmg_solve(nmg_hierarchy* h, const double* b, double* x, const nmg_sol
  * max_slots requests in flight.  nmg_submit queues a solve of A x = b on
  * hierarchy h and returns a ticket at once; b and x (FP64, host or device, b
  * ready when submitted) must stay valid until the request completes.  A
- * request starts when a slot is free, its hierarchy runs no other request and
- * the budget allows; running requests advance concurrently on their
- * hierarchies' streams, so requests that arrive while others run join them.
+ * request starts when a slot is free, its hierarchy runs no other request (or
+ * has an idle extra workspace, see nmg_server_set_workspaces) and the budget
+ * allows; running requests advance concurrently on their own streams, so
+ * requests that arrive while others run join them.
  * Results equal those of nmg_solve.  nmg_poll returns NMG_PENDING at once
  * (timeout_ms <= 0) or waits up to timeout_ms and then returns NMG_ERR_TIMEOUT;
  * once a request is done it returns the solve's status, fills *info (ms_total
@@ -179,6 +180,14 @@ nmg_status nmg_solve(nmg_hierarchy* h, const double* b, double* x, const nmg_sol
  * nmg_solve on a hierarchy while the server may run a request on it.
  * NMG_ERR_OOM from nmg_submit if h alone exceeds the budget. */
 nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server** out);
+/* Lets up to extra_per_hierarchy further requests on the same hierarchy run at
+ * once (default 0).  Each one runs on a workspace the server allocates on first
+ * need and keeps until it stops: the hierarchy's vectors, Krylov bases, device
+ * scalars and stream, sharing its matrices, masks and patch inverses.  Results
+ * are the same as on the hierarchy itself.  The budget counts each such
+ * workspace; one is made only when the budget holds it.  NMG_ERR_INVALID for a
+ * count outside 0..1024. */
+nmg_status nmg_server_set_workspaces(nmg_server* s, int extra_per_hierarchy);
 nmg_status nmg_submit(nmg_server* s, nmg_hierarchy* h, const double* b, double* x,
                       const nmg_solve_opts* opts, uint64_t* ticket);
 nmg_status nmg_poll(nmg_server* s, uint64_t ticket, int timeout_ms, nmg_solve_info* info);

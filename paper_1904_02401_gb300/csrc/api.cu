@@ -1058,6 +1058,112 @@ static void free_all(Hierarchy* h) {
     if (h->desc.stream == nullptr && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// The work buffers of one solve on h: V-cycle vectors and per-patch
+// corrections of every level and precision (FP32 and BF16 share the float
+// ones), the FGMRES workspace on the finest level (the Krylov bases come later,
+// sized by the restart length), the device scalars and flags, and their pinned
+// host mirrors.  The operator (matrices, masks, inverses) is allocated apart.
+static nmg_status alloc_workspace(Hierarchy* h) {
+    nmg_status st;
+    const bool low = (h->prec_mask & ((1 << NMG_PREC_FP32) | (1 << NMG_PREC_BF16))) != 0;
+    for (int l = 0; l < h->L; ++l) {
+        Level& Lv = h->lev[l];
+        const Geom& g = Lv.g;
+        const int64_t nvec = g.nodes * g.nc;
+        void* fvec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        if (low) {
+            for (int q = 0; q < 3; ++q)
+                if ((st = dalloc(h, &fvec[q], nvec * sizeof(float))) != NMG_OK) return st;
+            if ((st = dalloc(h, &fvec[4], nvec * sizeof(float))) != NMG_OK) return st;
+            for (int q : {3, 5})
+                if (l > 0 && (st = dalloc(h, &fvec[q], (size_t)g.patches * g.np * sizeof(float))) != NMG_OK) return st;
+        }
+        for (int p = 0; p < 3; ++p) {
+            if (!(h->prec_mask & (1 << p))) continue;
+            PrecData& P = Lv.p[p];
+            if (p == NMG_PREC_FP64) {
+                for (void** q : {&P.b, &P.x, &P.r, &P.x2})
+                    if ((st = dalloc(h, q, nvec * sizeof(double))) != NMG_OK) return st;
+                for (void** q : {&P.corr, &P.corr2})
+                    if (l > 0 && (st = dalloc(h, q, (size_t)g.patches * g.np * sizeof(double))) != NMG_OK) return st;
+            } else {
+                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3]; P.x2 = fvec[4]; P.corr2 = fvec[5];
+            }
+        }
+    }
+    const Geom& gf = h->lev[h->L - 1].g;
+    const int64_t n = gf.nodes * gf.nc;
+    for (double** q : {&h->b64, &h->x64, &h->w64})
+        if ((st = dalloc(h, (void**)q, n * sizeof(double))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->partial, (size_t)(kMaxRestart + 2) * kDotBlocks * sizeof(double))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->scal, S_COUNT * sizeof(double))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->flags, FLAG_COUNT * sizeof(int))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->pbar, 2 * sizeof(unsigned))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->counters, 4 * sizeof(unsigned))) != NMG_OK) return st;
+    if ((st = dalloc(h, (void**)&h->cyc, 4 * sizeof(int))) != NMG_OK) return st;
+    if (cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) != cudaSuccess) return fail(NMG_ERR_CUDA, "memset");
+    if (cudaMemset(h->flags, 0, FLAG_COUNT * sizeof(int)) != cudaSuccess) return fail(NMG_ERR_CUDA, "memset");
+    if (cudaMemset(h->pbar, 0, 2 * sizeof(unsigned)) != cudaSuccess) return fail(NMG_ERR_CUDA, "memset");
+    if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->host_cyc, 4 * sizeof(int)) != cudaSuccess)
+        return fail(NMG_ERR_OOM, "pinned host allocation failed");
+    return NMG_OK;
+}
+
+// A second solve workspace for base: its own work buffers and stream, and
+// base's matrices, masks, patch inverses and coarse inverse (read-only during
+// solves), so that two requests on one hierarchy run at the same time with the
+// same kernels on the same data (bitwise the same results).  budget: bytes the
+// workspace may take (0 = unlimited).  The autotuner's choices are copied.
+static nmg_status clone_workspace(Hierarchy* base, size_t budget, Hierarchy** out) {
+    *out = nullptr;
+    auto* h = new nmg_hierarchy();
+    h->desc = base->desc;
+    h->desc.stream = nullptr;
+    h->desc.mem_budget_bytes = budget;
+    h->dim = base->dim;
+    h->nc = base->nc;
+    h->L = base->L;
+    h->prec_mask = base->prec_mask;
+    h->n0 = base->n0;
+    h->coarse_inv = base->coarse_inv;
+    for (int l = 0; l < h->L; ++l) {
+        Level& Lv = h->lev[l];
+        const Level& B = base->lev[l];
+        Lv.g = B.g;
+        Lv.ready = B.ready;
+        Lv.A64 = B.A64;
+        Lv.mask = B.mask;
+        for (int p = 0; p < 3; ++p) {
+            Lv.p[p].A = B.p[p].A;
+            Lv.p[p].inv = B.p[p].inv;
+            Lv.p[p].inv_stride = B.p[p].inv_stride;
+        }
+    }
+    for (int p = 0; p < 3; ++p) {
+        h->engine_choice[p] = base->engine_choice[p];
+        h->auto_tail[p] = base->auto_tail[p];
+        h->auto_tile[p] = base->auto_tile[p];
+        h->tail_patches[p] = base->tail_patches[p];
+        h->tile_patches[p] = base->tile_patches[p];
+        h->fused[p] = base->fused[p];
+        std::memcpy(h->engine_key[p], base->engine_key[p], sizeof(h->engine_key[p]));
+    }
+    h->loop_mode = base->loop_mode;
+    nmg_status st = NMG_OK;
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+        st = fail(NMG_ERR_CUDA, "stream creation failed");
+    if (st == NMG_OK) st = alloc_workspace(h);
+    if (st != NMG_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return NMG_OK;
+}
+
 nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if (!d || !out) return fail(NMG_ERR_INVALID, "NULL argument");
     *out = nullptr;
@@ -1108,7 +1214,7 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
         }
     }
     const bool low = (h->prec_mask & ((1 << NMG_PREC_FP32) | (1 << NMG_PREC_BF16))) != 0;
-    for (int l = 0; l < L; ++l) {
+    for (int l = 0; l < L; ++l) {   // the operator: matrices, masks, patch inverses
         Level& Lv = h->lev[l];
         const Geom& g = Lv.g;
         const int64_t nvec = g.nodes * g.nc;
@@ -1119,52 +1225,18 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
             return cleanup(fail(NMG_ERR_CUDA, "mask upload failed"));
         float* A32 = nullptr;
         if (low && (st = dalloc(h, (void**)&A32, mat * sizeof(float))) != NMG_OK) return cleanup(st);
-        void* fvec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // float work vectors shared by FP32 / BF16
-        if (low) {
-            if ((st = dalloc(h, &fvec[4], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
-            for (int q = 0; q < 3; ++q)
-                if ((st = dalloc(h, &fvec[q], nvec * sizeof(float))) != NMG_OK) return cleanup(st);
-            for (int q : {3, 5})
-                if (l > 0 && (st = dalloc(h, &fvec[q], (size_t)g.patches * g.np * sizeof(float))) != NMG_OK)
-                    return cleanup(st);
-        }
         for (int p = 0; p < 3; ++p) {
             if (!(h->prec_mask & (1 << p))) continue;
             PrecData& P = Lv.p[p];
-            if (p == NMG_PREC_FP64) {
-                P.A = Lv.A64;
-                for (void** q : {&P.b, &P.x, &P.r, &P.x2})
-                    if ((st = dalloc(h, q, nvec * sizeof(double))) != NMG_OK) return cleanup(st);
-                for (void** q : {&P.corr, &P.corr2})
-                    if (l > 0 && (st = dalloc(h, q, (size_t)g.patches * g.np * sizeof(double))) != NMG_OK)
-                        return cleanup(st);
-            } else {
-                P.A = A32;
-                P.b = fvec[0]; P.x = fvec[1]; P.r = fvec[2]; P.corr = fvec[3]; P.x2 = fvec[4]; P.corr2 = fvec[5];
-            }
+            P.A = p == NMG_PREC_FP64 ? (void*)Lv.A64 : (void*)A32;
             if (l > 0) {
                 P.inv_stride = pad16((int64_t)g.np * g.np, store_size(p));
                 if ((st = dalloc(h, &P.inv, (size_t)g.patches * P.inv_stride * store_size(p))) != NMG_OK) return cleanup(st);
             }
         }
     }
-    const Geom& gf = h->lev[L - 1].g;
-    const int64_t n = gf.nodes * gf.nc;
     if ((st = dalloc(h, (void**)&h->coarse_inv, (size_t)h->n0 * h->n0 * sizeof(double))) != NMG_OK) return cleanup(st);
-    for (double** q : {&h->b64, &h->x64, &h->w64})
-        if ((st = dalloc(h, (void**)q, n * sizeof(double))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->partial, (size_t)(kMaxRestart + 2) * kDotBlocks * sizeof(double))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->scal, S_COUNT * sizeof(double))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->flags, FLAG_COUNT * sizeof(int))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->pbar, 2 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->counters, 4 * sizeof(unsigned))) != NMG_OK) return cleanup(st);
-    if ((st = dalloc(h, (void**)&h->cyc, 4 * sizeof(int))) != NMG_OK) return cleanup(st);
-    if (cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
-    if (cudaMemset(h->flags, 0, FLAG_COUNT * sizeof(int)) != cudaSuccess) return cleanup(fail(NMG_ERR_CUDA, "memset"));
-    if (cudaMallocHost((void**)&h->host_scal, 16 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->host_flags, (FLAG_COUNT + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&h->host_cyc, 4 * sizeof(int)) != cudaSuccess)
-        return cleanup(fail(NMG_ERR_OOM, "pinned host allocation failed"));
+    if ((st = alloc_workspace(h)) != NMG_OK) return cleanup(st);
     *out = h;
     return NMG_OK;
 }
@@ -1472,7 +1544,8 @@ namespace nmg {
 
 struct Request {
     uint64_t ticket = 0;
-    Hierarchy* h = nullptr;
+    Hierarchy* h = nullptr;       // the hierarchy the request was submitted on
+    Hierarchy* slot = nullptr;    // where it runs: h itself or a workspace clone of h
     const double* b = nullptr;
     double* x = nullptr;
     nmg_solve_opts o{};
@@ -1495,17 +1568,39 @@ struct Server {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
+    // workspace clones per hierarchy (server thread only), kept until the server stops;
+    // at most extra_workspaces per hierarchy (0: one request per hierarchy at a time)
+    std::unordered_map<Hierarchy*, std::vector<Hierarchy*>> clones;
+    size_t clone_bytes = 0;
+    int extra_workspaces = 0;
+};
+
+// Memory the running requests hold: each hierarchy with a running request
+// once (its operator and first workspace), plus every workspace clone.
+struct Residency {
+    std::unordered_map<Hierarchy*, int> running;   // requests per submitted hierarchy
+    size_t bytes = 0;
+    void add(Hierarchy* h) {
+        if (running[h]++ == 0) bytes += h->bytes;
+    }
+    void remove(Hierarchy* h) {
+        if (--running[h] == 0) {
+            bytes -= h->bytes;
+            running.erase(h);
+        }
+    }
+    size_t with(Hierarchy* h) const { return running.count(h) ? 0 : h->bytes; }   // bytes h would add
 };
 
 static void finish_request(Server* S, Request* r, std::vector<Request*>& active, std::unordered_set<Hierarchy*>& busy,
-                           size_t& active_bytes) {
+                           Residency& res) {
     job_info(r->job, &r->info);
     r->info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count();
     r->err = r->job.err;
     if (r->ev) cudaEventDestroy(r->ev);
     r->ev = nullptr;
-    busy.erase(r->h);
-    active_bytes -= r->h->bytes;
+    busy.erase(r->slot);
+    res.remove(r->h);
     active.erase(std::find(active.begin(), active.end(), r));
     std::lock_guard<std::mutex> lk(S->mu);
     r->done = true;
@@ -1515,8 +1610,8 @@ static void finish_request(Server* S, Request* r, std::vector<Request*>& active,
 static void server_loop(Server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> active;
-    std::unordered_set<Hierarchy*> busy;
-    size_t active_bytes = 0;
+    std::unordered_set<Hierarchy*> busy;   // slots (hierarchies or clones) running a request
+    Residency res;
     for (;;) {
         std::vector<Request*> admit;
         {
@@ -1526,12 +1621,40 @@ static void server_loop(Server* S) {
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
             }
+            // in arrival order: a request starts on its hierarchy, or on an idle clone of it, or on a
+            // new clone if the budget holds one more workspace; otherwise it waits
+            S->clone_bytes = 0;
+            for (auto& kv : S->clones)
+                for (Hierarchy* c : kv.second) S->clone_bytes += c->bytes;
             for (auto it = S->queue.begin(); it != S->queue.end() && (int)(active.size() + admit.size()) < S->max_slots;) {
                 Request* r = *it;
-                const bool fits = S->budget == 0 || active_bytes + r->h->bytes <= S->budget || active.empty();
-                if (!busy.count(r->h) && fits) {
-                    busy.insert(r->h);
-                    active_bytes += r->h->bytes;
+                const size_t used = res.bytes + S->clone_bytes;
+                const size_t need = res.with(r->h);
+                const bool fits = S->budget == 0 || used + need <= S->budget || (active.empty() && admit.empty());
+                Hierarchy* slot = nullptr;
+                if (fits) {
+                    if (!busy.count(r->h)) slot = r->h;
+                    for (size_t c = 0; !slot && c < S->clones[r->h].size(); ++c)
+                        if (!busy.count(S->clones[r->h][c])) slot = S->clones[r->h][c];
+                    if (!slot && (int)S->clones[r->h].size() < S->extra_workspaces) {
+                        const size_t room = S->budget == 0 ? 0 : (S->budget > used + need ? S->budget - used - need : 1);
+                        Hierarchy* c = nullptr;
+                        if (clone_workspace(r->h, room, &c) == NMG_OK) {
+                            if (ensure_krylov(c, r->o.restart) == NMG_OK) {   // the Krylov bases inside the budget too
+                                c->desc.mem_budget_bytes = 0;
+                                S->clones[r->h].push_back(c);
+                                slot = c;
+                            } else {
+                                free_all(c);
+                                delete c;
+                            }
+                        }
+                    }
+                }
+                if (slot) {
+                    busy.insert(slot);
+                    res.add(r->h);
+                    r->slot = slot;
                     admit.push_back(r);
                     it = S->queue.erase(it);
                 } else {
@@ -1542,9 +1665,9 @@ static void server_loop(Server* S) {
         for (Request* r : admit) {
             active.push_back(r);
             const int64_t l0 = g_launches;
-            nmg_status st = job_start(r->job, r->h, r->b, r->x, r->o);
+            nmg_status st = job_start(r->job, r->slot, r->b, r->x, r->o);
             if (st == NMG_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) == cudaSuccess) {
-                cudaEventRecord(r->ev, r->h->stream);
+                cudaEventRecord(r->ev, r->slot->stream);
             } else {
                 if (st == NMG_OK) st = fail(NMG_ERR_CUDA, "event creation failed");
                 r->job.st = st;
@@ -1569,12 +1692,12 @@ static void server_loop(Server* S) {
                     const int64_t l0 = g_launches;
                     job_advance(r->job);
                     r->job.launches += g_launches - l0;
-                    if (r->job.phase != SolveJob::P_DONE) cudaEventRecord(r->ev, r->h->stream);
+                    if (r->job.phase != SolveJob::P_DONE) cudaEventRecord(r->ev, r->slot->stream);
                 }
             }
             if (r->job.phase == SolveJob::P_DONE) {
-                cudaStreamSynchronize(r->h->stream);
-                finish_request(S, r, active, busy, active_bytes);
+                cudaStreamSynchronize(r->slot->stream);
+                finish_request(S, r, active, busy, res);
                 progressed = true;
                 continue;
             }
@@ -1596,6 +1719,15 @@ nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server*
     cudaGetDevice(&S->device);
     S->worker = std::thread(nmg::server_loop, S);
     *out = reinterpret_cast<nmg_server*>(S);
+    return NMG_OK;
+}
+
+nmg_status nmg_server_set_workspaces(nmg_server* server, int extra_per_hierarchy) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S || extra_per_hierarchy < 0 || extra_per_hierarchy > 1024)
+        return fail(NMG_ERR_INVALID, "bad server or workspace count");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->extra_workspaces = extra_per_hierarchy;
     return NMG_OK;
 }
 
@@ -1657,6 +1789,12 @@ nmg_status nmg_server_destroy(nmg_server* server) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto& kv : S->by_ticket) delete kv.second;
+    for (auto& kv : S->clones)
+        for (nmg::Hierarchy* c : kv.second) {
+            cudaStreamSynchronize(c->stream);
+            free_all(c);
+            delete c;
+        }
     delete S;
     return NMG_OK;
 }

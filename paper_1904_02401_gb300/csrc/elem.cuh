@@ -73,70 +73,113 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
 // acc = (A x)_i for node i (stencil layout), summed over the stencil positions
 // in ascending order and, inside a block, over the columns; the values of x at
 // the neighbour j = i + (dx, dy, dz) come from xval(j, dx, dy, dz, xv) (loaded,
-// converted, recomputed or read from a shared-memory tile).
-template <typename T, int DIM, class XF, bool GLOBAL_A = true>
+// converted, recomputed or read from a shared-memory tile).  The loads of G
+// consecutive stencil positions are issued before their products (an absent
+// neighbour reads the node itself and a zero of the padded matrix, and its
+// terms are skipped), so a thread waits for one memory round trip per group,
+// not per position; the products are the same terms in the same order.
+// GB = 0 picks G: 9 for a 2d matrix in global memory, else 1 (a matrix in
+// shared memory has no latency to hide; in 3d the 16-entry blocks already give
+// each position 16 independent loads, and grouping measured slower on GB300);
+// kernels with few registers per thread pass a smaller G.
+template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0>
 __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ A, XF&& xval, int64_t i,
                                            T (&acc)[DIM + 1]) {
     constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
+    constexpr int G = GB > 0 ? GB : (GLOBAL_A && DIM == 2) ? 9 : 1;
+    static_assert(NST % G == 0, "stencil positions per load group must divide the stencil");
     int ix, iy, iz;
     node_xyz(g, i, ix, iy, iz);
     const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
 #pragma unroll
     for (int r = 0; r < NC; ++r) acc[r] = T(0);
+    if constexpr (G == 1) {   // one position at a time, its loads only when the neighbour exists
 #pragma unroll
-    for (int s = 0; s < NST; ++s) {
-        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
-        const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
-                        (iz + dz >= 0) && (iz + dz < g.nn[2]);
-        if (ok) {
-            const int64_t j = i + dx + dy * sy + dz * sz;
-            T xv[NC];
-            xval(j, dx, dy, dz, xv);
+        for (int s = 0; s < NST; ++s) {
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+            const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                            (iz + dz >= 0) && (iz + dz < g.nn[2]);
+            if (ok) {
+                const int64_t j = i + dx + dy * sy + dz * sz;
+                T xv[NC];
+                xval(j, dx, dy, dz, xv);
+                const T* As = A + (int64_t)s * NB * g.ld + i;
+#pragma unroll
+                for (int r = 0; r < NC; ++r)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const T* a = As + (int64_t)(r * NC + c) * g.ld;
+                        T av;
+                        if constexpr (GLOBAL_A) av = __ldg(a);
+                        else av = *a;
+                        acc[r] = fma(av, xv[c], acc[r]);
+                    }
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int s0 = 0; s0 < NST; s0 += G) {
+        T av[G][NB], xv[G][NC];
+        bool okv[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int s = s0 + q;
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+            const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                            (iz + dz >= 0) && (iz + dz < g.nn[2]);
+            okv[q] = ok;
+            const int64_t j = ok ? i + dx + dy * sy + dz * sz : i;
+            xval(j, ok ? dx : 0, ok ? dy : 0, ok ? dz : 0, xv[q]);
             const T* As = A + (int64_t)s * NB * g.ld + i;
 #pragma unroll
-            for (int r = 0; r < NC; ++r)
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const T* a = As + (int64_t)(r * NC + c) * g.ld;
-                    T av;
-                    if constexpr (GLOBAL_A) av = __ldg(a);
-                    else av = *a;
-                    acc[r] = fma(av, xv[c], acc[r]);
-                }
+            for (int e = 0; e < NB; ++e) {
+                if constexpr (GLOBAL_A) av[q][e] = __ldg(As + (int64_t)e * g.ld);
+                else av[q][e] = As[(int64_t)e * g.ld];
+            }
         }
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+            if (okv[q])
+#pragma unroll
+                for (int r = 0; r < NC; ++r)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[r] = fma(av[q][r * NC + c], xv[q][c], acc[r]);
     }
 }
 
 // y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
 // at a node j come from xval(j, xv) (loaded, converted or recomputed).
-template <typename T, int DIM, class XF, bool GLOBAL_A = true>
+template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0>
 __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
                                             const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     constexpr int NC = DIM + 1;
     T acc[NC];
     auto xv4 = [&](int64_t j, int, int, int, T* xv) { xval(j, xv); };
-    spmv_acc_f<T, DIM, decltype(xv4)&, GLOBAL_A>(g, A, xv4, i, acc);
+    spmv_acc_f<T, DIM, decltype(xv4)&, GLOBAL_A, GB>(g, A, xv4, i, acc);
 #pragma unroll
     for (int r = 0; r < NC; ++r) y[i * NC + r] = residual ? b[i * NC + r] - acc[r] : acc[r];
 }
 
 // y_i = (A x)_i or b_i - (A x)_i with x stored as TX (converted to T on load);
 // GLOBAL_A = false when A lives in shared memory.
-template <typename T, int DIM, typename TX = T, bool GLOBAL_A = true>
+template <typename T, int DIM, typename TX = T, bool GLOBAL_A = true, int GB = 0>
 __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const TX* __restrict__ x,
                                           const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     auto xval = [&](int64_t j, T* xv) {
 #pragma unroll
         for (int c = 0; c < DIM + 1; ++c) xv[c] = widen<T, TX>(x[j * (DIM + 1) + c]);
     };
-    spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A>(g, A, xval, b, y, residual, i);
+    spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A, GB>(g, A, xval, b, y, residual, i);
 }
 
 // Row r of node i of y = A x or b - A x: the same terms in the same order as
 // row r of spmv_node (stencil positions ascending, then block columns), so the
 // value is bitwise equal; lets a kernel spread a node's rows over threads.
+// In 2d the loads of the 9 stencil positions are issued before their
+// products (in 3d one position at a time measured faster).
 template <typename T, int DIM>
 __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i,
@@ -144,21 +187,51 @@ __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A,
     constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
+    constexpr int G = DIM == 2 ? 9 : 1;
     int ix, iy, iz;
     node_xyz(g, i, ix, iy, iz);
     const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
     T acc = T(0);
+    if constexpr (G == 1) {   // one position at a time, its loads only when the neighbour exists
 #pragma unroll
-    for (int s = 0; s < NST; ++s) {
-        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
-        const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
-                        (iz + dz >= 0) && (iz + dz < g.nn[2]);
-        if (ok) {
-            const int64_t j = i + dx + dy * sy + dz * sz;
+        for (int s = 0; s < NST; ++s) {
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+            const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                            (iz + dz >= 0) && (iz + dz < g.nn[2]);
+            if (ok) {
+                const int64_t j = i + dx + dy * sy + dz * sz;
+                const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), x[j * NC + c], acc);
+            }
+        }
+        y[i * NC + r] = residual ? b[i * NC + r] - acc : acc;
+        return;
+    }
+#pragma unroll
+    for (int s0 = 0; s0 < NST; s0 += G) {
+        T av[G][NC], xv[G][NC];
+        bool okv[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const int s = s0 + q;
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+            const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                            (iz + dz >= 0) && (iz + dz < g.nn[2]);
+            okv[q] = ok;
+            const int64_t j = ok ? i + dx + dy * sy + dz * sz : i;
             const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), x[j * NC + c], acc);
+            for (int c = 0; c < NC; ++c) {
+                av[q][c] = __ldg(As + (int64_t)c * g.ld);
+                xv[q][c] = x[j * NC + c];
+            }
         }
+#pragma unroll
+        for (int q = 0; q < G; ++q)
+            if (okv[q])
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc = fma(av[q][c], xv[q][c], acc);
     }
     y[i * NC + r] = residual ? b[i * NC + r] - acc : acc;
 }
@@ -231,27 +304,50 @@ __device__ __forceinline__ void vanka_update_value(const Geom& g, const T* __res
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int c = xyz[k];
-        if (k >= DIM) { cp[k][0] = 0; cl[k][0] = 0; cnt[k] = 1; continue; }
-        if (c & 1) { cp[k][0] = (c - 1) >> 1; cl[k][0] = 1; cnt[k] = 1; }
-        else {
-            int n = 0;
-            if (c > 0) { cp[k][n] = (c >> 1) - 1; cl[k][n] = 2; ++n; }
-            if (c < g.cells[k]) { cp[k][n] = c >> 1; cl[k][n] = 0; ++n; }
-            cnt[k] = n;
+        if (k >= DIM) { cp[k][0] = cp[k][1] = 0; cl[k][0] = cl[k][1] = 0; cnt[k] = 1; continue; }
+        if (c & 1) {   // inside one patch
+            cp[k][0] = cp[k][1] = (c - 1) >> 1;
+            cl[k][0] = cl[k][1] = 1;
+            cnt[k] = 1;
+        } else {       // on a patch boundary: the lower patch (if any) first, then the upper
+            const bool lo = c > 0, hi = c < g.cells[k];
+            cp[k][0] = lo ? (c >> 1) - 1 : c >> 1;
+            cl[k][0] = lo ? 2 : 0;
+            cp[k][1] = c >> 1;
+            cl[k][1] = 0;
+            cnt[k] = (int)lo + (int)hi;
         }
     }
+    // the corrections of the (at most 2^d) patches are loaded first (an absent
+    // patch reads the first one again), then summed in ascending patch order
+    constexpr int NZ = DIM == 3 ? 2 : 1;
+    T cv[NZ][2][2][NC];
+#pragma unroll
+    for (int a = 0; a < NZ; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const bool pres = a < cnt[2] && b < cnt[1] && e < cnt[0];
+                const int ea = pres ? a : 0, eb = pres ? b : 0, ee = pres ? e : 0;
+                const int64_t p = cp[0][ee] + (int64_t)g.pc[0] * (cp[1][eb] + (int64_t)g.pc[1] * cp[2][ea]);
+                const int loc = cl[0][ee] + 3 * cl[1][eb] + 9 * cl[2][ea];
+                const T* cpn = corr + p * NP + loc * NC;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) cv[a][b][e][c] = cpn[c];
+            }
     T sum[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) sum[c] = T(0);
-    for (int a = 0; a < cnt[2]; ++a)
-        for (int b = 0; b < cnt[1]; ++b)
-            for (int e = 0; e < cnt[0]; ++e) {
-                const int64_t p = cp[0][e] + (int64_t)g.pc[0] * (cp[1][b] + (int64_t)g.pc[1] * cp[2][a]);
-                const int loc = cl[0][e] + 3 * cl[1][b] + 9 * cl[2][a];
-                const T* cpn = corr + p * NP + loc * NC;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) sum[c] += cpn[c];
-            }
+    for (int a = 0; a < NZ; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (a < cnt[2] && b < cnt[1] && e < cnt[0])
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) sum[c] += cv[a][b][e][c];
     const int m = cnt[0] * cnt[1] * cnt[2];
     const T wgt = average ? omega / T(m) : omega;
 #pragma unroll
@@ -295,21 +391,34 @@ __device__ __forceinline__ void restrict_value_f(const Geom& f, const Geom& c, R
     node_xyz(c, I, X, Y, Z);
 #pragma unroll
     for (int k = 0; k < NC; ++k) sum[k] = T(0);
+    // per plane of fine nodes: the 3 x 3 values are loaded first (an absent node
+    // reads the centre again), then summed in order with their weights
     const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+#pragma unroll
     for (int oz = zlo; oz <= zhi; ++oz) {
         const int fz = 2 * Z + oz;
         if (fz < 0 || fz >= f.nn[2]) continue;
-        for (int oy = -1; oy <= 1; ++oy) {
-            const int fy = 2 * Y + oy;
-            if (fy < 0 || fy >= f.nn[1]) continue;
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int fx = 2 * X + ox;
-                if (fx < 0 || fx >= f.nn[0]) continue;
-                const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+        T rv[3][3][NC];
+        bool in[3][3];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) sum[k] = fma(w, rval(fx, fy, fz, k), sum[k]);
+        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int fy = 2 * Y + oy, fx = 2 * X + ox;
+                const bool ok = fy >= 0 && fy < f.nn[1] && fx >= 0 && fx < f.nn[0];
+                in[oy + 1][ox + 1] = ok;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) rv[oy + 1][ox + 1][k] = rval(ok ? fx : 2 * X, ok ? fy : 2 * Y, fz, k);
             }
-        }
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox)
+                if (in[oy + 1][ox + 1]) {
+                    const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) sum[k] = fma(w, rv[oy + 1][ox + 1][k], sum[k]);
+                }
     }
 }
 
@@ -341,21 +450,37 @@ __device__ __forceinline__ void prolong_value(const Geom& f, const Geom& c, cons
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int v = xyz[k];
-        if (k >= DIM || !(v & 1)) { ci[k][0] = v >> 1; cnt[k] = 1; }
+        if (k >= DIM || !(v & 1)) { ci[k][0] = ci[k][1] = v >> 1; cnt[k] = 1; }
         else { ci[k][0] = (v - 1) >> 1; ci[k][1] = (v + 1) >> 1; cnt[k] = 2; }
     }
+    // the (at most 2^d) coarse values are loaded first, then summed in order
+    constexpr int NZ = DIM == 3 ? 2 : 1;
+    T ev[NZ][2][2][NC];
+#pragma unroll
+    for (int a = 0; a < NZ; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int64_t I = ci[0][e] + (int64_t)c.nn[0] * (ci[1][b] + (int64_t)c.nn[1] * ci[2][a]);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) ev[a][b][e][k] = ec[I * NC + k];
+            }
     T sum[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) sum[k] = T(0);
-    for (int a = 0; a < cnt[2]; ++a)
-        for (int b = 0; b < cnt[1]; ++b)
-            for (int e = 0; e < cnt[0]; ++e) {
-                const T w = (cnt[0] == 2 ? T(0.5) : T(1)) * (cnt[1] == 2 ? T(0.5) : T(1)) *
-                            (cnt[2] == 2 ? T(0.5) : T(1));
-                const int64_t I = ci[0][e] + (int64_t)c.nn[0] * (ci[1][b] + (int64_t)c.nn[1] * ci[2][a]);
 #pragma unroll
-                for (int k = 0; k < NC; ++k) sum[k] = fma(w, ec[I * NC + k], sum[k]);
-            }
+    for (int a = 0; a < NZ; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (a < cnt[2] && b < cnt[1] && e < cnt[0]) {
+                    const T w = (cnt[0] == 2 ? T(0.5) : T(1)) * (cnt[1] == 2 ? T(0.5) : T(1)) *
+                                (cnt[2] == 2 ? T(0.5) : T(1));
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) sum[k] = fma(w, ev[a][b][e][k], sum[k]);
+                }
 #pragma unroll
     for (int k = 0; k < NC; ++k) v[k] = fmask[i * NC + k] ? x_in[i * NC + k] : x_in[i * NC + k] + sum[k];
 }

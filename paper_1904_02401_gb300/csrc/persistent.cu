@@ -152,7 +152,7 @@ struct VCycle {
         phase(a, cx, L.small, [&] {
             const Range r = threads(L.small);
             for (int64_t i = r.first; i < L.g.nodes; i += r.step)
-                spmv_node<T, DIM>(L.g, (const T*)L.A, (const T*)L.x, (const T*)L.b, (T*)L.r, true, i);
+                spmv_node<T, DIM, T, true, 1>(L.g, (const T*)L.A, (const T*)L.x, (const T*)L.b, (T*)L.r, true, i);
         });
     }
 

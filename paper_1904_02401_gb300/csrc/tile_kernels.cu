@@ -174,15 +174,16 @@ k_tile_step(const __grid_constant__ TileArgs<T, TS> a) {
                 for (int c = 0; c < NC; ++c) sd[ld * NC + c] = a.b[i * NC + c];
             } else {
                 const int lc = (gx - x0[0]) + RX * ((gy - x0[1]) + RX * (gz - x0[2]));
-                T acc[NC];
-                spmv_acc_f<T, DIM>(
-                    g, a.A,
-                    [&](int64_t, int dx, int dy, int dz, T* xv) {
-                        const int l = lc + dx + RX * (dy + RX * dz);
+                auto sxval = [&](int64_t, int dx, int dy, int dz, T* xv) {
+                    const int l = lc + dx + RX * (dy + RX * dz);
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) xv[c] = sx[l * NC + c];
-                    },
-                    i, acc);
+                    for (int c = 0; c < NC; ++c) xv[c] = sx[l * NC + c];
+                };
+                T acc[NC];
+                // x comes from shared memory; in 2d the matrix loads of 3 stencil positions
+                // are in flight together (a larger group does not fit the 512-thread register
+                // budget)
+                spmv_acc_f<T, DIM, decltype(sxval)&, true, DIM == 2 ? 3 : 1>(g, a.A, sxval, i, acc);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) sd[ld * NC + c] = a.b[i * NC + c] - acc[c];
             }

@@ -130,3 +130,45 @@ def test_memory_budget_admission(pool):
         assert nmg.nmg_submit(server, S.handle, b, x, solve_opts(), t) == nmg.NMG_ERR_OOM
     finally:
         nmg.nmg_server_destroy(server)
+
+
+def test_same_hierarchy_requests_overlap(pool):
+    """With extra workspaces allowed, requests on one hierarchy run at the same
+    time on workspace clones (own vectors and stream, shared matrices and
+    inverses); every result is
+    bitwise the one nmg_solve gives alone, and the mixed-precision and FP64
+    requests on the same clone keep their own iteration counts."""
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    s, S = pool[1]
+    reqs = [((1, 0)[i % 3 == 0], 300 + i) for i in range(12)]
+    alone = []
+    for prec, seed in reqs:
+        b = _rhs(s, seed)
+        x = torch.empty_like(b)
+        info = S.solve(b, x, precision=prec, engine=nmg.NMG_ENGINE_KERNELS)
+        assert info.status == 0
+        alone.append((x.clone(), info.iterations))
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(0, 6, server))
+    nmg.check(nmg.nmg_server_set_workspaces(server, 5))
+    assert nmg.nmg_server_set_workspaces(server, -1) == nmg.NMG_ERR_INVALID
+    try:
+        for rnd in range(2):   # the second round reuses the clones the first one made
+            bufs, tickets = [], []
+            for prec, seed in reqs:
+                b = _rhs(s, seed)
+                bufs.append((b, torch.zeros_like(b)))
+            torch.cuda.synchronize()
+            for (prec, seed), (b, x) in zip(reqs, bufs):
+                t = C.c_uint64()
+                nmg.check(nmg.nmg_submit(server, S.handle, b, x,
+                                         solve_opts(precision=prec, engine=nmg.NMG_ENGINE_KERNELS), t))
+                tickets.append(t.value)
+            for i, t in enumerate(tickets):
+                info = nmg.nmg_solve_info()
+                assert nmg.nmg_poll(server, t, 60000, info) == 0, nmg.nmg_last_error()
+                assert torch.equal(bufs[i][1], alone[i][0]), (rnd, i)
+                assert info.iterations == alone[i][1]
+    finally:
+        nmg.nmg_server_destroy(server)
