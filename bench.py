@@ -327,6 +327,21 @@ def gpu_arm(args):
         S.solve(bh, xh, precision=args.precision, use_graph=use_graph)
         e2e.append(1000.0 * (time.perf_counter() - t))
 
+    # set-up of the finest level for a new Jacobian (BSR already on the device): patch extraction
+    # and FP64 Gauss-Jordan inversion of every patch, stored in the prepared precisions
+    fin = sysm.fine
+    rp_d = torch.from_numpy(np.ascontiguousarray(fin.row_ptr, dtype=np.int64)).cuda()
+    ci_d = torch.from_numpy(np.ascontiguousarray(fin.col_idx, dtype=np.int32)).cuda()
+    v_d = torch.from_numpy(np.ascontiguousarray(fin.vals, dtype=np.float64)).cuda()
+    set_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        nmg.check(nmg.nmg_set_jacobian(S.handle, sysm.problem.levels - 1, fin.nodes, ci_d.numel(), rp_d, ci_d, v_d, 1))
+        torch.cuda.synchronize()
+        set_ms.append(1000.0 * (time.perf_counter() - t))
+    del rp_d, ci_d, v_d
+
     ms = statistics.mean(times)
     ms_max, wall_max = max_over_ranks([ms, wall], dist, "cuda")
 
@@ -379,6 +394,7 @@ def gpu_arm(args):
                      "bytes_per_launch": kbytes,
                      "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
         "spmv": _spmv_line(sprof, hbm, args.steps),
+        "setup": _setup_line(sysm, statistics.median(set_ms)),
         "vcycle": {"ms": vms / vcount if vcount else None, "bytes": vbytes,
                    "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
                    "engine": {1: "per-step kernels", 2: "persistent kernel",
@@ -416,6 +432,27 @@ def _spmv_line(prof, hbm, steps):
     return {"kernel": "k_spmv / k_spmv_rows (finest-level residual product)", "bound": "hbm", "achieved": gbs,
             "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "launch_ms": ms / cnt, "bytes_per_launch": nbytes,
             "timed": f"{cnt} launches over {steps} solves (events around each launch)"}
+
+
+# FP64 peak of one GB300 derived from its units and clock: 152 SMs x 2 FP64 FMA
+# lanes per SM clock x 2 flops x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def _setup_line(sysm, ms):
+    """Re-factorisation of the finest level (nmg_set_jacobian from device
+    buffers): Gauss-Jordan inversion of every n_p x n_p patch, n_p^3 FP64 FMAs
+    each, against the FP64 ALU peak."""
+    d = sysm.problem.dim
+    patches = 1
+    for nk in sysm.problem.n:
+        patches *= nk // 2
+    n_p = 3 ** d * (d + 1)
+    gflops = 2.0 * patches * n_p ** 3 / (ms * 1e-3) / 1e9
+    return {"what": "nmg_set_jacobian of the finest level: stencil copy, FP32 copy, patch extraction and FP64 "
+                    "Gauss-Jordan inversion of every patch (median of 3)", "ms": ms, "patches": patches, "n_p": n_p,
+            "bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+            "frac": gflops / FP64_PEAK_GFLOPS}
 
 
 def _matvec(sysm, x):

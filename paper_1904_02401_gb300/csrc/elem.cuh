@@ -78,17 +78,19 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
 // neighbour reads the node itself and a zero of the padded matrix, and its
 // terms are skipped), so a thread waits for one memory round trip per group,
 // not per position; the products are the same terms in the same order.
-// GB = 0 picks G: 9 for a 2d matrix in global memory, else 1 (a matrix in
-// shared memory has no latency to hide; in 3d the 16-entry blocks already give
-// each position 16 independent loads, and grouping measured slower on GB300);
-// kernels with few registers per thread pass a smaller G.
+// GB = 0 picks G: for a 2d matrix in global memory 9 (FP32) or 3 (FP64: 9
+// positions of 9 doubles and 3 neighbour values take over 200 registers), else
+// 1 (a matrix in shared memory has no latency to hide; in 3d the 16-entry
+// blocks already give each position 16 independent loads, and grouping
+// measured slower on GB300); kernels with few registers per thread pass a
+// smaller G.
 template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0>
 __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ A, XF&& xval, int64_t i,
                                            T (&acc)[DIM + 1]) {
     constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
-    constexpr int G = GB > 0 ? GB : (GLOBAL_A && DIM == 2) ? 9 : 1;
+    constexpr int G = GB > 0 ? GB : (GLOBAL_A && DIM == 2) ? (sizeof(T) == 8 ? 3 : 9) : 1;
     static_assert(NST % G == 0, "stencil positions per load group must divide the stencil");
     int ix, iy, iz;
     node_xyz(g, i, ix, iy, iz);

@@ -159,7 +159,7 @@ __device__ __forceinline__ double finish_row(const double* __restrict__ partial,
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int b = lane + 32 * r;
-        v[r] = b < kDotBlocks ? partial[(int64_t)k * kDotBlocks + b] : 0.0;
+        v[r] = b < kDotBlocks ? __ldcg(partial + (int64_t)k * kDotBlocks + b) : 0.0;
     }
     double s = 0.0;
 #pragma unroll
@@ -295,22 +295,24 @@ __device__ __forceinline__ void dots_all(const double* __restrict__ V, int64_t l
 
 // In the last block: out[k] = sum over the blocks of the partials of value k
 // (warp w sums the blocks w, w + kMdWarps, ..., then the warps are added).
+// Launched on kDotBlocks blocks: a lane's loads are all issued before they are
+// summed (one memory round trip for the whole tail).
 __device__ void finish_chunks(const double* __restrict__ partial, int nvec, double* __restrict__ out, int lane,
                               int warp) {
     __shared__ double fs[kMdWarps][kMdChunk];
-    const int G = gridDim.x;
+    constexpr int G = kDotBlocks;
+    constexpr int PER = (G + kMdWarps - 1) / kMdWarps;
     for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
         const double* p = partial + (int64_t)chunk * G * kMdChunk + lane;
-        double s = 0.0;
-        int b = warp;
-        for (; b + 7 * kMdWarps < G; b += 8 * kMdWarps) {
-            double v[8];
+        double v[PER];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = p[(int64_t)(b + u * kMdWarps) * kMdChunk];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < PER; ++u) {
+            const int b = warp + u * kMdWarps;
+            v[u] = b < G ? __ldcg(p + (int64_t)b * kMdChunk) : 0.0;
         }
-        for (; b < G; b += kMdWarps) s += p[(int64_t)b * kMdChunk];
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) s += v[u];
         fs[warp][lane] = s;
         __syncthreads();
         if (warp == 0 && c0 + lane < nvec) {
@@ -397,12 +399,14 @@ k_gs_update_dot_norm(const double* __restrict__ V, int64_t ldv, const int* __res
     }
     dots_all(V, ldv, nvec, w, lo, hi, partial, lane, warp);
     if (!last_block(counter)) return;
-    finish_chunks(partial, nvec, scal + S_Y, lane, warp);
+    finish_chunks(partial, nvec, scal + S_Y, lane, warp);   // ends with a block barrier
     if (warp == 0) {
         const double t = finish_row(partial, kNormRow, lane);
+        // ||h2||^2 by the warp: lane l squares h2_l and h2_{l+32}, then a fixed shuffle tree
+        double hh = 0.0;
+        for (int k = lane; k < nvec; k += 32) hh = fma(scal[S_Y + k], scal[S_Y + k], hh);
+        for (int off = 16; off > 0; off >>= 1) hh += __shfl_down_sync(0xffffffffu, hh, off);
         if (lane == 0) {
-            double hh = 0.0;
-            for (int k = 0; k < nvec; ++k) hh = fma(scal[S_Y + k], scal[S_Y + k], hh);
             const double d = t - hh;
             s_hnext = d > 0.0 ? sqrt(d) : 0.0;
             scal[S_HC + j + 1] = s_hnext;

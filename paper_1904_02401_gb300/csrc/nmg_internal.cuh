@@ -16,7 +16,7 @@ namespace nmg {
 constexpr int kMaxLevels = 16;
 constexpr int kMaxRestart = 64;
 constexpr int kMaxDevices = 64;       // per-device caches of launch shapes
-constexpr int kDotBlocks = 296;        // fixed grid of the deterministic reductions (2 x 148)
+constexpr int kDotBlocks = 304;        // fixed grid of the deterministic reductions (2 per SM of a GB300's 152)
 
 // ---------------------------------------------------------------------------
 // Structured level geometry (uniform Q1 mesh, nodes x fastest)

@@ -19,9 +19,11 @@ using namespace elem;
 constexpr int kWaitSpins = 1 << 22;
 constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CTA
 
-// y = A x  or  y = b - A x, one thread per node.  A in stencil layout.
+// y = A x  or  y = b - A x, one thread per node.  A in stencil layout.  Two
+// CTAs per SM (at most 128 registers a thread): the finest 2d level's 259 CTAs
+// then run in one wave with every thread's stencil loads in flight together.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
 k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
        T* __restrict__ y, bool residual) {
     NMG_PDL_ENTRY();
