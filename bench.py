@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="serving workload: Poisson stream of solves over resident 2d/3d hierarchies")
     ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--mesh", default=None,
+                    help="serving: one mesh only, e.g. 2d:128 or 3d:32 (many right-hand sides on one hierarchy)")
+    ap.add_argument("--workspaces", type=int, default=0,
+                    help="serving: extra concurrent requests per hierarchy (nmg_server_set_workspaces)")
     ap.add_argument("--profile-range", action="store_true",
                     help="after the warm-up, run one solve between cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off) and exit")
@@ -487,10 +491,15 @@ def serving_arm(args):
 
     torch.cuda.set_device(0)
     sizes = [(2, 64), (2, 128), (2, 256), (2, 512), (3, 16), (3, 32), (3, 64)]
+    seeds = (10, 12)
+    if args.mesh:
+        d, nn = args.mesh.split(":")
+        sizes = [(int(d[0]), int(nn))]
+        seeds = (10,)
     pool = []
     t0 = time.time()
     for dim, n in sizes:
-        for cseed in (10, 12):
+        for cseed in seeds:
             levels = int(np.log2(n)) - 1
             p = Problem(dim=dim, n=(n,) * dim, levels=levels,
                         solid=(0, +1, 0.6) if dim == 2 else (2, -1, 0.25), conv_seed=cseed)
@@ -510,7 +519,7 @@ def serving_arm(args):
         out = []
         for i in range(count):
             d2 = rng.random() < 0.5
-            cands = [k for k, (dim, n, S, m) in enumerate(pool) if (dim == 2) == d2]
+            cands = [k for k, (dim, n, S, m) in enumerate(pool) if (dim == 2) == d2 or args.mesh]
             k = int(rng.choice(cands))
             dim, n, S, mask = pool[k]
             g = torch.Generator(device="cuda").manual_seed(seed0 + 2 * i)
@@ -522,6 +531,7 @@ def serving_arm(args):
 
     server = C.c_void_p()
     nmg.check(nmg.nmg_server_create(budget, 16, server))
+    nmg.check(nmg.nmg_server_set_workspaces(server, args.workspaces))
 
     def run(reqs, rate):
         tickets = []
@@ -558,9 +568,13 @@ def serving_arm(args):
         "metric": METRIC, "value": statistics.median(lat), "unit": "ms (p50 submit-to-completion latency)",
         "n_gpus": 1, "steps": len(reqs), "warmup": 20, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "serving: Poisson stream of condensed-momentum solves, 2d 64^2-512^2 and 3d "
-                               "16^3-64^3 (50/50), 14 resident hierarchies, FP32 V-cycle / FP64 FGMRES(30), "
-                               "rtol 1e-8, memory budget 150 GB, 16 slots",
+        "config": {"workload": ("serving: Poisson stream of condensed-momentum solves, 2d 64^2-512^2 and 3d "
+                                "16^3-64^3 (50/50), 14 resident hierarchies, FP32 V-cycle / FP64 FGMRES(30), "
+                                "rtol 1e-8, memory budget 150 GB, 16 slots") if not args.mesh else
+                               (f"serving: Poisson stream of condensed-momentum solves on one resident {args.mesh} "
+                                "hierarchy (right-hand sides seeded per request), FP32 V-cycle / FP64 FGMRES(30), "
+                                "rtol 1e-8, memory budget 150 GB, 16 slots"),
+                   "extra_workspaces_per_hierarchy": args.workspaces,
                    "arrival_rate_per_s": rate, "saturated_solves_per_s": saturated},
         "p50_ms": statistics.median(lat), "p99_ms": lat_sorted[max(0, int(0.99 * len(lat)) - 1)],
         "solves_per_s": len(reqs) / wall, "failed": bad, "mean_iterations": statistics.mean(its),
