@@ -36,7 +36,26 @@ WORKLOADS = {
              "4 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
     "cfg4": ("3d 96^3 Q1 condensed-momentum Jacobian (3,650,692 unknowns), solid z<0.25, "
              "6 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
+    # the ALE-extension solve (problem (3)) on the same meshes: d displacement components per node
+    "ale2": ("2d 256x256 Q1 ALE-extension operator (vector Laplacian on the fluid, 132,098 unknowns), "
+             "solid x>0.6 fixed, 7 MG levels, V(2,2) Vanka 2x2-cell patches (18 unknowns), FGMRES(30) rtol 1e-8"),
+    "ale3": ("3d 32^3 Q1 ALE-extension operator (vector Laplacian on the fluid, 107,811 unknowns), "
+             "solid z<0.25 fixed, 4 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), FGMRES(30) rtol 1e-8"),
+    "ale4": ("3d 96^3 Q1 ALE-extension operator (vector Laplacian on the fluid, 2,738,019 unknowns), "
+             "solid z<0.25 fixed, 6 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), FGMRES(30) rtol 1e-8"),
 }
+# the mesh each ALE workload shares with a condensed-momentum workload
+ALE_BASE = {"ale2": "cfg2", "ale3": "cfg3", "ale4": "cfg4"}
+
+
+def load_workload(name):
+    """The seeded synthetic system of a workload and its unknowns per node."""
+    from gen import build_ale_system, build_system, config_problem
+    if name in ALE_BASE:
+        p = config_problem(ALE_BASE[name])
+        return build_ale_system(p), p.dim
+    p = config_problem(name)
+    return build_system(p), p.dim + 1
 # DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
 # capture of the current kernel source (profiles/k_vanka_apply_*.md); a
 # workload or precision without a capture of the current source reports null.
@@ -163,9 +182,9 @@ class ClockSampler:
 CHILD = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
-from gen import build_system, config_problem
+from bench import load_workload
 from oracle.solver import OracleSolver
-s = build_system(config_problem({wl!r}))
+s, _ = load_workload({wl!r})
 o = OracleSolver(s.levels, s.dirichlet)
 times = []
 info = None
@@ -239,15 +258,14 @@ def gpu_arm(args):
     else:
         dist = None
 
-    from gen import build_system, config_problem
     from paper_1904_02401_gb300 import nmg
     from paper_1904_02401_gb300.session import Session, solve_opts
 
-    sysm = build_system(config_problem(WORKLOAD))
+    sysm, ncomp = load_workload(WORKLOAD)
     stream = torch.cuda.Stream()
     prec_mask = (1 << nmg.NMG_PREC_FP64) | (1 << args.precision)
     S = Session(sysm.problem.dim, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels], sysm.dirichlet,
-                precisions=prec_mask, stream=stream.cuda_stream)
+                precisions=prec_mask, stream=stream.cuda_stream, ncomp=ncomp)
     n = sysm.unknowns
     b = torch.from_numpy(sysm.rhs).cuda()
     x = torch.empty_like(b)
@@ -389,7 +407,8 @@ def gpu_arm(args):
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
                       "speedup_of_mixed": statistics.mean(t64) / ms},
-        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 else "k_vanka_apply_ring") +
+        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 or WORKLOAD in ALE_BASE
+                                else "k_vanka_apply_ring") +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
@@ -451,7 +470,7 @@ def _setup_line(sysm, ms):
     patches = 1
     for nk in sysm.problem.n:
         patches *= nk // 2
-    n_p = 3 ** d * (d + 1)
+    n_p = 3 ** d * int(sysm.fine.vals.shape[1])
     gflops = 2.0 * patches * n_p ** 3 / (ms * 1e-3) / 1e9
     return {"what": "nmg_set_jacobian of the finest level: stencil copy, FP32 copy, patch extraction and FP64 "
                     "Gauss-Jordan inversion of every patch (median of 3)", "ms": ms, "patches": patches, "n_p": n_p,

@@ -242,6 +242,23 @@ def _slices(pos, cells):
     return tuple(slice(p, p + nk) for p, nk in zip(reversed(pos), reversed(cells)))
 
 
+def solid_cells(problem: Problem, cells: tuple, coarse_cells: Optional[tuple] = None) -> np.ndarray:
+    """Cell classification (array order z, y, x): solid iff the centroid of the
+    cell's ancestor on the coarsest level lies in the solid region, so that
+    every level resolves the same interface (item (II) of Section 4.3)."""
+    h = 1.0 / cells[0]
+    cshape = tuple(reversed(cells))
+    if coarse_cells is None:
+        coarse_cells = level_cells(problem)[0]
+    r = cells[0] // coarse_cells[0]
+    axes = [((np.arange(nk) // r) + 0.5) * r * h for nk in cells]
+    cent = np.meshgrid(*reversed(axes), indexing="ij")[::-1]   # list over x, y, z
+    if problem.solid is None:
+        return np.zeros(cshape, dtype=bool)
+    ax, sign, thr = problem.solid
+    return sign * (cent[ax] - thr) > 0
+
+
 def assemble_level(problem: Problem, cells: tuple, conv: Optional[Callable] = None,
                    solid_mask: Optional[np.ndarray] = None,
                    coarse_cells: Optional[tuple] = None) -> LevelMatrix:
@@ -260,19 +277,8 @@ def assemble_level(problem: Problem, cells: tuple, conv: Optional[Callable] = No
     cshape = tuple(reversed(cells))
     nst = 3 ** dim
 
-    # cell classification by the centroid of the cell's ancestor on the coarsest
-    # level, so that every level resolves the same interface (item (II))
     if solid_mask is None:
-        if coarse_cells is None:
-            coarse_cells = level_cells(problem)[0]
-        r = cells[0] // coarse_cells[0]
-        axes = [((np.arange(nk) // r) + 0.5) * r * h for nk in cells]
-        cent = np.meshgrid(*reversed(axes), indexing="ij")[::-1]   # list over x, y, z
-        if problem.solid is None:
-            solid_mask = np.zeros(cshape, dtype=bool)
-        else:
-            ax, sign, thr = problem.solid
-            solid_mask = sign * (cent[ax] - thr) > 0
+        solid_mask = solid_cells(problem, cells, coarse_cells)
     fluid = (~solid_mask).astype(np.float64)
     solid = solid_mask.astype(np.float64)
 
@@ -318,7 +324,16 @@ def assemble_level(problem: Problem, cells: tuple, conv: Optional[Callable] = No
     for i in range(dim):
         S[..., center, i, i][bnd] = 1.0
 
-    # BSR conversion: keep every in-range stencil block (the Q1 node-adjacency pattern)
+    return _stencil_to_bsr(S, dim, cells, nc)
+
+
+def _stencil_to_bsr(S: np.ndarray, dim: int, cells: tuple, nc: int) -> LevelMatrix:
+    """BSR conversion of a node-stencil array S[nodes (z, y, x), s, nc, nc]:
+    keep every in-range stencil block (the Q1 node-adjacency pattern)."""
+    nodes_n = tuple(nk + 1 for nk in cells)
+    nshape = tuple(reversed(nodes_n))
+    nst = 3 ** dim
+    offs = _offsets(dim)
     nodes = int(np.prod(nodes_n))
     valid = np.zeros(nshape + (nst,), dtype=bool)
     for s, o in enumerate(offs):
@@ -335,7 +350,6 @@ def assemble_level(problem: Problem, cells: tuple, conv: Optional[Callable] = No
     node_ids, s_ids = np.nonzero(valid)
     col_idx = (node_ids + lin[s_ids]).astype(np.int32)
     vals = S.reshape(nodes, nst, nc, nc)[valid]
-    del S
     return LevelMatrix(cells=tuple(cells), row_ptr=row_ptr, col_idx=col_idx,
                        vals=np.ascontiguousarray(vals))
 
@@ -389,6 +403,88 @@ def build_system(problem: Problem) -> SyntheticSystem:
     mats = [assemble_level(problem, c, conv=conv) for c in level_cells(problem)]
     fine = mats[-1]
     mask = dirichlet_mask(problem.dim, fine.cells, problem.outflow)
+    rng = np.random.default_rng(problem.rhs_seed)
+    rhs = rng.uniform(-1.0, 1.0, size=mask.shape[0])
+    rhs[mask.astype(bool)] = 0.0
+    return SyntheticSystem(problem=problem, levels=mats, rhs=rhs, dirichlet=mask)
+
+
+# ----------------------------------------------------------------------------
+# ALE extension (problem (3) of Section 4.2): n_c = d
+# ----------------------------------------------------------------------------
+
+def ale_fixed_nodes(dim: int, cells: tuple, solid_mask: np.ndarray) -> np.ndarray:
+    """Nodes whose deformation is given in the extension problem: the mesh
+    boundary (the outer walls do not move) and every node of a solid cell
+    (there the deformation is the solid's own, from problem (2)).  Array order
+    (z, y, x)."""
+    nodes_n = tuple(nk + 1 for nk in cells)
+    fixed = _dirichlet_nodes(dim, cells)
+    for a in range(2 ** dim):
+        pa = tuple((a >> m) & 1 for m in range(dim))
+        fixed[_slices(pa, cells)] |= solid_mask
+    assert fixed.shape == tuple(reversed(nodes_n))
+    return fixed
+
+
+def assemble_ale_level(problem: Problem, cells: tuple, coarse_cells: Optional[tuple] = None) -> LevelMatrix:
+    """The ALE-extension operator on one level: the harmonic extension of the
+    solid deformation into the fluid, one Q1 Laplacian per displacement
+    component, (grad u_c, grad phi_c) summed over the fluid cells (2^d-point
+    Gauss quadrature).  Rows and columns of the fixed nodes (ale_fixed_nodes)
+    are those of the identity; their given values enter through the
+    right-hand side."""
+    dim = problem.dim
+    nc = dim
+    na = 2 ** dim
+    h = 1.0 / cells[0]
+    nodes_n = tuple(nk + 1 for nk in cells)
+    nshape = tuple(reversed(nodes_n))
+    nst = 3 ** dim
+    solid = solid_cells(problem, cells, coarse_cells)
+    fluid = (~solid).astype(np.float64)
+    _, w, psi, dpsi = reference_element(dim)
+    G = h ** (dim - 2) * np.einsum("q,qam,qbm->ab", w, dpsi, dpsi)
+    eye = np.eye(nc)
+    S = np.zeros(nshape + (nst, nc, nc))
+    for a in range(na):
+        pa = tuple((a >> m) & 1 for m in range(dim))
+        rows = _slices(pa, cells)
+        for b in range(na):
+            pb = tuple((b >> m) & 1 for m in range(dim))
+            s = sum((pb[m] - pa[m] + 1) * 3 ** m for m in range(dim))
+            S[rows + (s,)] += (fluid * G[a, b])[..., None, None] * eye
+    fixed = ale_fixed_nodes(dim, cells, solid)
+    S[fixed] = 0.0
+    offs = _offsets(dim)
+    for s, o in enumerate(offs):
+        src, dst = [], []
+        for m in reversed(range(dim)):
+            lo = max(0, -o[m])
+            hi = nodes_n[m] - max(0, o[m])
+            dst.append(slice(lo, hi))
+            src.append(slice(lo + o[m], hi + o[m]))
+        colf = np.zeros(nshape, dtype=bool)
+        colf[tuple(dst)] = fixed[tuple(src)]
+        S[..., s, :, :][colf] = 0.0
+    center = (nst - 1) // 2
+    for i in range(nc):
+        S[..., center, i, i][fixed] = 1.0
+    return _stencil_to_bsr(S, dim, cells, nc)
+
+
+def ale_mask(problem: Problem, cells: tuple) -> np.ndarray:
+    """uint8 per unknown of the extension problem: 1 on every component of a fixed node."""
+    fixed = ale_fixed_nodes(problem.dim, cells, solid_cells(problem, cells))
+    return np.repeat(fixed.reshape(-1), problem.dim).astype(np.uint8)
+
+
+def build_ale_system(problem: Problem) -> SyntheticSystem:
+    """All level matrices of the ALE-extension problem (n_c = d), its seeded
+    right-hand side (numpy default_rng(rhs_seed).uniform(-1, 1), zero on the
+    fixed unknowns) and the fixed-unknown mask."""
+    mats = [assemble_ale_level(problem, c) for c in level_cells(problem)]
+    mask = ale_mask(problem, mats[-1].cells)
     rng = np.random.default_rng(problem.rhs_seed)
     rhs = rng.uniform(-1.0, 1.0, size=mask.shape[0])
     rhs[mask.astype(bool)] = 0.0

@@ -69,7 +69,10 @@ typedef struct {
     int n[3];                       /* finest-level cells per direction; n[2] ignored when dim==2 */
     int levels;                     /* multigrid levels >= 1; n[k] divisible by 2^(levels-1) and,
                                        above the coarsest level, even (patches of 2^dim cells)    */
-    int ncomp;                      /* must equal dim + 1                                          */
+    int ncomp;                      /* unknowns per node: dim + 1 for the condensed momentum system
+                                       (velocity, pressure; problem (1) of Section 4.2), or dim for
+                                       a vector problem such as the ALE extension (problem (3)); the
+                                       latter runs the KERNELS engine only                        */
     int patch_cells;                /* cells per patch direction; only 2 is supported              */
     const uint8_t* dirichlet_mask;  /* host, one byte per finest-level unknown, 1 = Dirichlet;
                                        coarse-level masks are taken by injection (node I <- 2I)   */

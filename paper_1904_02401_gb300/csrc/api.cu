@@ -36,10 +36,10 @@ static nmg_status fail(nmg_status st, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));                    \
     } while (0)
 
-static Geom make_geom(int dim, const int* cells) {
+static Geom make_geom(int dim, int nc, const int* cells) {
     Geom g{};
     g.dim = dim;
-    g.nc = dim + 1;
+    g.nc = nc;
     g.nodes = 1;
     g.patches = 1;
     for (int k = 0; k < 3; ++k) {
@@ -510,6 +510,15 @@ static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) 
 // The fastest is kept per precision and (nu1, nu2, weighting).
 static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* engine) {
     const int prec = o.precision;
+    if (h->nc == h->dim) {   // n_c = d (vector problems): per-step kernels only, no cluster tail, no tiles
+        if (o.engine != NMG_ENGINE_AUTO && o.engine != NMG_ENGINE_KERNELS)
+            return fail(NMG_ERR_INVALID, "hierarchies with ncomp = dim run the KERNELS engine only");
+        h->tail_patches[prec] = 0;
+        h->tile_patches[prec] = 0;
+        h->fused[prec] = 0;
+        *engine = NMG_ENGINE_KERNELS;
+        return NMG_OK;
+    }
     if (o.engine != NMG_ENGINE_AUTO) {
         h->tail_patches[prec] = o.engine == NMG_ENGINE_PERSISTENT ? 0 : o.tail_patches;
         h->tile_patches[prec] = o.engine == NMG_ENGINE_KERNELS ? o.tile_patches : 0;
@@ -1168,7 +1177,7 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if (!d || !out) return fail(NMG_ERR_INVALID, "NULL argument");
     *out = nullptr;
     if (d->dim != 2 && d->dim != 3) return fail(NMG_ERR_INVALID, "dim must be 2 or 3");
-    if (d->ncomp != d->dim + 1) return fail(NMG_ERR_INVALID, "ncomp must be dim + 1");
+    if (d->ncomp != d->dim + 1 && d->ncomp != d->dim) return fail(NMG_ERR_INVALID, "ncomp must be dim + 1 or dim");
     if (d->patch_cells != 2) return fail(NMG_ERR_INVALID, "only patch_cells = 2 is supported");
     if (d->levels < 1 || d->levels > kMaxLevels) return fail(NMG_ERR_INVALID, "levels out of range");
     if (!d->dirichlet_mask) return fail(NMG_ERR_INVALID, "dirichlet_mask is NULL");
@@ -1192,7 +1201,7 @@ nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if (d->stream) h->stream = (cudaStream_t)d->stream;
     else if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(fail(NMG_ERR_CUDA, "stream creation failed"));
-    for (int l = 0; l < L; ++l) h->lev[l].g = make_geom(d->dim, cells[l]);
+    for (int l = 0; l < L; ++l) h->lev[l].g = make_geom(d->dim, d->ncomp, cells[l]);
     const Geom& c0 = h->lev[0].g;
     h->n0 = c0.nodes * c0.nc;
     if (h->n0 > 2048) return cleanup(fail(NMG_ERR_INVALID, "coarsest level too large for the dense solve (> 2048 unknowns)"));

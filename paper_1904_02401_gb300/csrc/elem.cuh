@@ -84,10 +84,9 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
 // blocks already give each position 16 independent loads, and grouping
 // measured slower on GB300); kernels with few registers per thread pass a
 // smaller G.
-template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0>
+template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0, int NC>
 __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ A, XF&& xval, int64_t i,
-                                           T (&acc)[DIM + 1]) {
-    constexpr int NC = DIM + 1;
+                                           T (&acc)[NC]) {
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
     constexpr int G = GB > 0 ? GB : (GLOBAL_A && DIM == 2) ? (sizeof(T) == 8 ? 3 : 9) : 1;
@@ -154,10 +153,9 @@ __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ 
 
 // y_i = (A x)_i or b_i - (A x)_i for node i (stencil layout); the values of x
 // at a node j come from xval(j, xv) (loaded, converted or recomputed).
-template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0>
+template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0, int NC = DIM + 1>
 __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__ A, XF&& xval,
                                             const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
-    constexpr int NC = DIM + 1;
     T acc[NC];
     auto xv4 = [&](int64_t j, int, int, int, T* xv) { xval(j, xv); };
     spmv_acc_f<T, DIM, decltype(xv4)&, GLOBAL_A, GB>(g, A, xv4, i, acc);
@@ -167,14 +165,14 @@ __device__ __forceinline__ void spmv_node_f(const Geom& g, const T* __restrict__
 
 // y_i = (A x)_i or b_i - (A x)_i with x stored as TX (converted to T on load);
 // GLOBAL_A = false when A lives in shared memory.
-template <typename T, int DIM, typename TX = T, bool GLOBAL_A = true, int GB = 0>
+template <typename T, int DIM, typename TX = T, bool GLOBAL_A = true, int GB = 0, int NC = DIM + 1>
 __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A, const TX* __restrict__ x,
                                           const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i) {
     auto xval = [&](int64_t j, T* xv) {
 #pragma unroll
-        for (int c = 0; c < DIM + 1; ++c) xv[c] = widen<T, TX>(x[j * (DIM + 1) + c]);
+        for (int c = 0; c < NC; ++c) xv[c] = widen<T, TX>(x[j * NC + c]);
     };
-    spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A, GB>(g, A, xval, b, y, residual, i);
+    spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A, GB, NC>(g, A, xval, b, y, residual, i);
 }
 
 // Row r of node i of y = A x or b - A x: the same terms in the same order as
@@ -182,11 +180,10 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
 // value is bitwise equal; lets a kernel spread a node's rows over threads.
 // In 2d the loads of the 9 stencil positions are issued before their
 // products (in 3d one position at a time measured faster).
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i,
                                          int r) {
-    constexpr int NC = DIM + 1;
     constexpr int NB = NC * NC;
     constexpr int NST = (DIM == 2) ? 9 : 27;
     constexpr int G = DIM == 2 ? 9 : 1;
@@ -239,9 +236,8 @@ __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A,
 }
 
 // Gathers R_p d into sd[0..NP) (called by one warp; lane-strided).
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void gather_patch(const Geom& g, const T* __restrict__ d, int64_t p, T* sd, int lane) {
-    constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     int px, py, pz;
     patch_xyz(g, p, px, py, pz);
@@ -253,9 +249,9 @@ __device__ __forceinline__ void gather_patch(const Geom& g, const T* __restrict_
 
 // corr_p = A_p^{-1} sd for one patch by one warp (lane owns rows lane + 32 q);
 // Ap: column-major inverse (global or shared memory).
-template <typename T, typename TS, int DIM, bool GLOBAL>
+template <typename T, typename TS, int DIM, bool GLOBAL, int NC = DIM + 1>
 __device__ __forceinline__ void apply_patch(const TS* Ap, const T* sd, T* __restrict__ corr_p, int lane) {
-    constexpr int NP = ((DIM == 2) ? 9 : 27) * (DIM + 1);
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     constexpr int NQ = (NP + 31) / 32;
     T acc[NQ];
 #pragma unroll
@@ -294,11 +290,10 @@ __device__ __forceinline__ void apply_patch(const TS* Ap, const T* sd, T* __rest
 // v = x_i + w_i * (sum of the corrections of the patches containing node i),
 // in ascending patch order; w_i = omega / multiplicity ("average") or omega;
 // x_i = 0 when x_zero (x is not read).
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void vanka_update_value(const Geom& g, const T* __restrict__ corr,
                                                    const T* __restrict__ x, bool x_zero, T omega, bool average,
                                                    int64_t i, T* v) {
-    constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     int xyz[3];
     node_xyz(g, i, xyz[0], xyz[1], xyz[2]);
@@ -360,13 +355,13 @@ __device__ __forceinline__ void vanka_update_value(const Geom& g, const T* __res
 }
 
 // x_out_i = x_in_i + w_i * sum of the corrections (x_in may equal x_out).
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void vanka_update_node(const Geom& g, const T* __restrict__ corr, const T* x_in,
                                                   T* x_out, bool x_zero, T omega, bool average, int64_t i) {
-    T v[DIM + 1];
-    vanka_update_value<T, DIM>(g, corr, x_in, x_zero, omega, average, i, v);
+    T v[NC];
+    vanka_update_value<T, DIM, NC>(g, corr, x_in, x_zero, omega, average, i, v);
 #pragma unroll
-    for (int c = 0; c < DIM + 1; ++c) x_out[i * (DIM + 1) + c] = v[c];
+    for (int c = 0; c < NC; ++c) x_out[i * NC + c] = v[c];
 }
 
 // Fused: x_out_i = update of x_in at node i (as above) and
@@ -385,10 +380,9 @@ __device__ __forceinline__ void update_residual_node(const Geom& g, const T* __r
 
 // sum = (P^T r_f)_I for coarse node I (Q1 full weighting), the fine values
 // coming from rval(fx, fy, fz, k) (global memory or a shared-memory tile).
-template <typename T, int DIM, class RF>
+template <typename T, int DIM, class RF, int NC>
 __device__ __forceinline__ void restrict_value_f(const Geom& f, const Geom& c, RF&& rval, int64_t I,
-                                                 T (&sum)[DIM + 1]) {
-    constexpr int NC = DIM + 1;
+                                                 T (&sum)[NC]) {
     int X, Y, Z;
     node_xyz(c, I, X, Y, Z);
 #pragma unroll
@@ -425,10 +419,9 @@ __device__ __forceinline__ void restrict_value_f(const Geom& f, const Geom& c, R
 }
 
 // (r_c)_I = (P^T r_f)_I, zero on coarse Dirichlet entries.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, const T* __restrict__ rf,
                                               T* __restrict__ rc, const uint8_t* __restrict__ cmask, int64_t I) {
-    constexpr int NC = DIM + 1;
     T sum[NC];
     restrict_value_f<T, DIM>(
         f, c,
@@ -441,11 +434,10 @@ __device__ __forceinline__ void restrict_node(const Geom& f, const Geom& c, cons
 }
 
 // v = x_in_i + (P e_c)_i, x_in_i on fine Dirichlet entries.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void prolong_value(const Geom& f, const Geom& c, const T* __restrict__ ec,
                                               const T* __restrict__ x_in, const uint8_t* __restrict__ fmask,
                                               int64_t i, T* v) {
-    constexpr int NC = DIM + 1;
     int xyz[3];
     node_xyz(f, i, xyz[0], xyz[1], xyz[2]);
     int ci[3][2], cnt[3];
@@ -488,13 +480,13 @@ __device__ __forceinline__ void prolong_value(const Geom& f, const Geom& c, cons
 }
 
 // (x_f)_i += (P e_c)_i, fine Dirichlet entries untouched.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __device__ __forceinline__ void prolong_node(const Geom& f, const Geom& c, const T* __restrict__ ec,
                                              T* __restrict__ xf, const uint8_t* __restrict__ fmask, int64_t i) {
-    T v[DIM + 1];
-    prolong_value<T, DIM>(f, c, ec, xf, fmask, i, v);
+    T v[NC];
+    prolong_value<T, DIM, NC>(f, c, ec, xf, fmask, i, v);
 #pragma unroll
-    for (int k = 0; k < DIM + 1; ++k) xf[i * (DIM + 1) + k] = v[k];
+    for (int k = 0; k < NC; ++k) xf[i * NC + k] = v[k];
 }
 
 // Fused: x_out_i = x_in_i + (P e_c)_i and r_i = b_i - (A x_out)_i with x_out at

@@ -329,13 +329,12 @@ __device__ void finish_chunks(const double* __restrict__ partial, int nvec, doub
 // Z_j = z (the V-cycle output xf, widened exactly to FP64), w = A z in FP64,
 // and out[k] = V_k . w for k <= j.  Each block first computes w on its share
 // of the nodes, then the dot products over the same unknowns.
-template <typename TX, int DIM>
+template <typename TX, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(kMdThreads)
 k_spmv_zstore_dots(Geom g, const double* __restrict__ A, const TX* __restrict__ xf, double* __restrict__ Z,
                    double* w, const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc,
                    double* __restrict__ partial, double* __restrict__ out, unsigned* counter) {
     NMG_PDL_ENTRY();
-    constexpr int NC = DIM + 1;
     const int j = cyc[0], nvec = j + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* z64 = Z + (int64_t)j * ldv;
@@ -503,12 +502,13 @@ void launch_spmv_zstore_dots(const Geom& g, const double* A, const TX* xf, doubl
                              int64_t ldv, const int* cyc, double* partial, double* out, unsigned* counter,
                              cudaStream_t s) {
     g_launches += 1;
+    const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
     if (g.dim == 2)
-        pdl_launch(k_spmv_zstore_dots<TX, 2>, dim3(kDotBlocks), dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc,
-                   partial, out, counter);
+        pdl_launch(lean ? k_spmv_zstore_dots<TX, 2, 2> : k_spmv_zstore_dots<TX, 2, 3>, dim3(kDotBlocks),
+                   dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc, partial, out, counter);
     else
-        pdl_launch(k_spmv_zstore_dots<TX, 3>, dim3(kDotBlocks), dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc,
-                   partial, out, counter);
+        pdl_launch(lean ? k_spmv_zstore_dots<TX, 3, 3> : k_spmv_zstore_dots<TX, 3, 4>, dim3(kDotBlocks),
+                   dim3(kMdThreads), 0, s, g, A, xf, Z, w, V, ldv, cyc, partial, out, counter);
 }
 template void launch_spmv_zstore_dots<float>(const Geom&, const double*, const float*, double*, double*,
                                              const double*, int64_t, const int*, double*, double*, unsigned*,

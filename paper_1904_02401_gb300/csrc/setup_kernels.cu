@@ -127,11 +127,10 @@ __device__ void gauss_jordan_smem(double* a, double* col, int* perm, int* s_piv,
 
 // Persistent launch over all patches of a level: gather A_i from the stencil
 // matrix, invert it, store A_i^{-1} column-major in every requested precision.
-template <int DIM>
+template <int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256)
 k_patch_invert(Geom g, const double* __restrict__ A, double* inv64, int64_t s64, float* inv32,
                int64_t s32, __nv_bfloat16* invbf, int64_t sbf, int* flags) {
-    constexpr int NC = DIM + 1;
     constexpr int NN = (DIM == 2) ? 9 : 27;      // nodes per patch
     constexpr int NP = NN * NC;
     constexpr int LDA = NP + 1;
@@ -308,15 +307,12 @@ cudaError_t launch_patch_invert(const Geom& g, const double* A64, double* inv64,
     if (grid > g.patches) grid = g.patches;
     if (grid < 1) return cudaSuccess;
     cudaError_t e;
-    if (g.dim == 2) {
-        e = cudaFuncSetAttribute(k_patch_invert<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_patch_invert<2><<<(unsigned)grid, 256, smem, s>>>(g, A64, inv64, s64, inv32, s32, invbf, sbf, flags);
-    } else {
-        e = cudaFuncSetAttribute(k_patch_invert<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_patch_invert<3><<<(unsigned)grid, 256, smem, s>>>(g, A64, inv64, s64, inv32, s32, invbf, sbf, flags);
-    }
+    const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
+    auto kern = g.dim == 2 ? (lean ? k_patch_invert<2, 2> : k_patch_invert<2, 3>)
+                           : (lean ? k_patch_invert<3, 3> : k_patch_invert<3, 4>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, 256, smem, s>>>(g, A64, inv64, s64, inv32, s32, invbf, sbf, flags);
     return cudaGetLastError();
 }
 

@@ -22,13 +22,13 @@ constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CT
 // y = A x  or  y = b - A x, one thread per node.  A in stencil layout.  Two
 // CTAs per SM (at most 128 registers a thread): the finest 2d level's 259 CTAs
 // then run in one wave with every thread's stencil loads in flight together.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 2)
 k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
        T* __restrict__ y, bool residual) {
     NMG_PDL_ENTRY();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < g.nodes) spmv_node<T, DIM>(g, A, x, b, y, residual, i);
+    if (i < g.nodes) spmv_node<T, DIM, T, true, 0, NC>(g, A, x, b, y, residual, i);
 }
 
 // The same product with one thread per (block row, node): thread t computes
@@ -37,15 +37,15 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
 // where a node's row work is long (3d: 108 terms per row; FP64), slower for
 // the 2d FP32 product, whose extra reads of x cost more than the added
 // parallelism gains.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 1)
 k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
             T* __restrict__ y, bool residual) {
     NMG_PDL_ENTRY();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= g.nodes * (DIM + 1)) return;
+    if (t >= g.nodes * NC) return;
     const uint32_t nodes = (uint32_t)g.nodes, r = (uint32_t)t / nodes;
-    spmv_row<T, DIM>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
+    spmv_row<T, DIM, NC>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
 }
 
 // corr_i = A_i^{-1} R_i d for every patch i: one warp per patch.  The patch
@@ -53,19 +53,19 @@ k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* _
 // consecutive entries (one coalesced 128-byte segment in FP32) and multiply
 // them by the broadcast d_j from shared memory; no cross-lane reduction.
 // Used for 3d patches (n_p = 108), where each warp streams 46.7 KB.
-template <typename T, typename TS, int DIM, int WARPS>
+template <typename T, typename TS, int DIM, int WARPS, int NC = DIM + 1>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
               T* __restrict__ corr) {
     NMG_PDL_ENTRY();
-    constexpr int NP = ((DIM == 2) ? 9 : 27) * (DIM + 1);
+    constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     __shared__ T sd[WARPS][NP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * WARPS + w;
     if (p >= g.patches) return;
-    gather_patch<T, DIM>(g, d, p, sd[w], lane);
+    gather_patch<T, DIM, NC>(g, d, p, sd[w], lane);
     __syncwarp();
-    apply_patch<T, TS, DIM, true>(inv + p * stride, sd[w], corr + p * NP, lane);
+    apply_patch<T, TS, DIM, true, NC>(inv + p * stride, sd[w], corr + p * NP, lane);
 }
 
 // Streaming apply for FP32 / BF16 inverses (2d and 3d): a persistent grid of
@@ -162,13 +162,13 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
 // x += w(node) * sum over the patches that contain the node of their
 // corrections (fixed order: ascending patch index), w = omega / multiplicity
 // ("average") or omega ("sum").  One thread per node, no atomics.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 1)
 k_vanka_update(Geom g, const T* __restrict__ corr, const T* x_in, T* x_out, bool x_zero, T omega,
                bool average) {
     NMG_PDL_ENTRY();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < g.nodes) vanka_update_node<T, DIM>(g, corr, x_in, x_out, x_zero, omega, average, i);
+    if (i < g.nodes) vanka_update_node<T, DIM, NC>(g, corr, x_in, x_out, x_zero, omega, average, i);
 }
 
 // Fused Vanka update and residual: x_out = x_in + w * corrections, r = b - A x_out
@@ -195,21 +195,21 @@ k_prolong_residual(Geom f, Geom c, const T* __restrict__ A, const T* __restrict_
 }
 
 // r_c = P^T r_f (Q1 full weighting), coarse Dirichlet entries zero.  One thread per coarse node.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 1)
 k_restrict(Geom f, Geom c, const T* __restrict__ rf, T* __restrict__ rc, const uint8_t* __restrict__ cmask) {
     NMG_PDL_ENTRY();
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (I < c.nodes) restrict_node<T, DIM>(f, c, rf, rc, cmask, I);
+    if (I < c.nodes) restrict_node<T, DIM, NC>(f, c, rf, rc, cmask, I);
 }
 
 // x_f += P e_c (Q1 interpolation), fine Dirichlet entries untouched.  One thread per fine node.
-template <typename T, int DIM>
+template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 1)
 k_prolong_add(Geom f, Geom c, const T* __restrict__ ec, T* __restrict__ xf, const uint8_t* __restrict__ fmask) {
     NMG_PDL_ENTRY();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < f.nodes) prolong_node<T, DIM>(f, c, ec, xf, fmask, i);
+    if (i < f.nodes) prolong_node<T, DIM, NC>(f, c, ec, xf, fmask, i);
 }
 
 // x = inv * b with the FP64 dense coarse inverse, one warp per row, FP64 sums.
@@ -255,12 +255,16 @@ cudaError_t wait_timeout_clear(cudaStream_t s) {
 template <typename T>
 void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual, cudaStream_t s) {
     g_launches += 1;
+    const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
     if (g.dim == 3)
-        pdl_launch(k_spmv_rows<T, 3>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
-    else if (sizeof(T) == 8)
-        pdl_launch(k_spmv_rows<T, 2>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
+        pdl_launch(lean ? k_spmv_rows<T, 3, 3> : k_spmv_rows<T, 3, 4>, dim3(blocks_for(g.nodes * g.nc, 256)),
+                   dim3(256), 0, s, g, A, x, b, y, residual);
+    else if constexpr (sizeof(T) == 8)
+        pdl_launch(lean ? k_spmv_rows<T, 2, 2> : k_spmv_rows<T, 2, 3>, dim3(blocks_for(g.nodes * g.nc, 256)),
+                   dim3(256), 0, s, g, A, x, b, y, residual);
     else
-        pdl_launch(k_spmv<T, 2>, dim3(blocks_for(g.nodes, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
+        pdl_launch(lean ? k_spmv<T, 2, 2> : k_spmv<T, 2, 3>, dim3(blocks_for(g.nodes, 256)), dim3(256), 0, s, g, A,
+                   x, b, y, residual);
 }
 
 // Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
@@ -295,7 +299,8 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     // layout (stride at most n_p^2 rounded up to 16 bytes); FP64 and other
     // layouts use the warp kernel
     const int np = g.dim == 2 ? 27 : 108;
-    const bool ring = sizeof(TS) <= 4 && ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
+    const bool lean = g.nc == g.dim;   // n_c = d: warp kernel (the ring's chunks are 27-row slices)
+    const bool ring = !lean && sizeof(TS) <= 4 && ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
                       stride >= (int64_t)np * np && stride * (int64_t)sizeof(TS) <= (int64_t)np * np * sizeof(TS) + 16;
     if (g.patches == 0) return;
     if constexpr (sizeof(TS) <= 4) {
@@ -310,15 +315,14 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
             return;
         }
     }
-    if (g.dim == 2) {
-        constexpr int W = 4;
-        const dim3 grid((unsigned)((g.patches + W - 1) / W));
-        pdl_launch(k_vanka_apply<T, TS, 2, W>, grid, dim3(W * 32), 0, s, g, inv, stride, d, corr);
-    } else {
-        constexpr int W = 4;
-        const dim3 grid((unsigned)((g.patches + W - 1) / W));
-        pdl_launch(k_vanka_apply<T, TS, 3, W>, grid, dim3(W * 32), 0, s, g, inv, stride, d, corr);
-    }
+    constexpr int W = 4;
+    const dim3 grid((unsigned)((g.patches + W - 1) / W));
+    if (g.dim == 2)
+        pdl_launch(lean ? k_vanka_apply<T, TS, 2, W, 2> : k_vanka_apply<T, TS, 2, W, 3>, grid, dim3(W * 32), 0, s, g,
+                   inv, stride, d, corr);
+    else
+        pdl_launch(lean ? k_vanka_apply<T, TS, 3, W, 3> : k_vanka_apply<T, TS, 3, W, 4>, grid, dim3(W * 32), 0, s, g,
+                   inv, stride, d, corr);
 }
 
 template <typename T>
@@ -331,8 +335,13 @@ void launch_vanka_update2(const Geom& g, const T* corr, const T* x_in, T* x_out,
                           cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(g.nodes, 256));
-    if (g.dim == 2) pdl_launch(k_vanka_update<T, 2>, grid, dim3(256), 0, s, g, corr, x_in, x_out, x_zero, omega, average);
-    else pdl_launch(k_vanka_update<T, 3>, grid, dim3(256), 0, s, g, corr, x_in, x_out, x_zero, omega, average);
+    const bool lean = g.nc == g.dim;
+    if (g.dim == 2)
+        pdl_launch(lean ? k_vanka_update<T, 2, 2> : k_vanka_update<T, 2, 3>, grid, dim3(256), 0, s, g, corr, x_in, x_out,
+                   x_zero, omega, average);
+    else
+        pdl_launch(lean ? k_vanka_update<T, 3, 3> : k_vanka_update<T, 3, 4>, grid, dim3(256), 0, s, g, corr, x_in, x_out,
+                   x_zero, omega, average);
 }
 
 template <typename T>
@@ -372,16 +381,18 @@ template <typename T>
 void launch_restrict(const Geom& f, const Geom& c, const T* rf, T* rc, const uint8_t* cmask, cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(c.nodes, 256));
-    if (f.dim == 2) pdl_launch(k_restrict<T, 2>, grid, dim3(256), 0, s, f, c, rf, rc, cmask);
-    else pdl_launch(k_restrict<T, 3>, grid, dim3(256), 0, s, f, c, rf, rc, cmask);
+    const bool lean = f.nc == f.dim;
+    if (f.dim == 2) pdl_launch(lean ? k_restrict<T, 2, 2> : k_restrict<T, 2, 3>, grid, dim3(256), 0, s, f, c, rf, rc, cmask);
+    else pdl_launch(lean ? k_restrict<T, 3, 3> : k_restrict<T, 3, 4>, grid, dim3(256), 0, s, f, c, rf, rc, cmask);
 }
 
 template <typename T>
 void launch_prolong_add(const Geom& f, const Geom& c, const T* ec, T* xf, const uint8_t* fmask, cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(f.nodes, 256));
-    if (f.dim == 2) pdl_launch(k_prolong_add<T, 2>, grid, dim3(256), 0, s, f, c, ec, xf, fmask);
-    else pdl_launch(k_prolong_add<T, 3>, grid, dim3(256), 0, s, f, c, ec, xf, fmask);
+    const bool lean = f.nc == f.dim;
+    if (f.dim == 2) pdl_launch(lean ? k_prolong_add<T, 2, 2> : k_prolong_add<T, 2, 3>, grid, dim3(256), 0, s, f, c, ec, xf, fmask);
+    else pdl_launch(lean ? k_prolong_add<T, 3, 3> : k_prolong_add<T, 3, 4>, grid, dim3(256), 0, s, f, c, ec, xf, fmask);
 }
 
 template <typename T>

@@ -28,10 +28,11 @@ class Session:
 
     levels: sequence (coarsest first) of (row_ptr int64, col_idx int32,
     vals float64 (nnzb, nc, nc)) host arrays; mask: uint8 finest-level
-    Dirichlet mask; precisions: bit mask of nmg.NMG_PREC_* (0 = all).
+    Dirichlet mask; precisions: bit mask of nmg.NMG_PREC_* (0 = all); ncomp:
+    unknowns per node, dim + 1 (default) or dim.
     """
 
-    def __init__(self, dim, n, levels, mask, precisions=0, stream=None, mem_budget=0, nlevels=None):
+    def __init__(self, dim, n, levels, mask, precisions=0, stream=None, mem_budget=0, nlevels=None, ncomp=None):
         self.dim = int(dim)
         self.n = tuple(int(v) for v in n)
         self._mask = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -40,7 +41,7 @@ class Session:
         for k in range(3):
             d.n[k] = self.n[k] if k < self.dim else 1
         d.levels = len(levels) if nlevels is None else int(nlevels)
-        d.ncomp = self.dim + 1
+        d.ncomp = self.dim + 1 if ncomp is None else int(ncomp)
         d.patch_cells = 2
         d.dirichlet_mask = self._mask.ctypes.data
         d.precisions = int(precisions)
