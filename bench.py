@@ -407,8 +407,7 @@ def gpu_arm(args):
         "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
         "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
                       "speedup_of_mixed": statistics.mean(t64) / ms},
-        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 or WORKLOAD in ALE_BASE
-                                else "k_vanka_apply_ring") +
+        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 else "k_vanka_apply_ring") +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
