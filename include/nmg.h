@@ -163,6 +163,25 @@ nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int6
 nmg_status nmg_solve(nmg_hierarchy* h, const double* b, double* x, const nmg_solve_opts* opts,
                      nmg_solve_info* info);
 
+/* Solves A x_k = b_k for k = 0..nrhs-1 against the same hierarchy (many
+ * right-hand sides per factorisation: the smoother is applied many hundred
+ * times per Jacobian, Section 5).  b and x hold nrhs FP64 vectors of
+ * ncomp * nodes entries, column k at offset k * ncomp * nodes, host or device.
+ * The columns run FGMRES in lockstep in groups of up to 8: every V-cycle
+ * serves all columns of the group that need one, reading each level matrix
+ * and each patch inverse once for all of them.  opts->precision must be
+ * NMG_PREC_FP32 or NMG_PREC_BF16 (the V-cycle's vectors are FP32); engine,
+ * tail and tile settings do not apply; use_graph != 0 replays the
+ * multi-vector V-cycle from a CUDA graph.  Each column's solution, iteration
+ * count and status equal those of nmg_solve on that column alone, bit for
+ * bit.  info: NULL or an array of nrhs records.  The columns after the first
+ * run on workspaces the hierarchy allocates on first need and keeps (vectors,
+ * Krylov bases and device scalars, sharing the operator), counted by
+ * nmg_hierarchy_bytes.  Returns the first failing column's status, else
+ * NMG_OK; NMG_ERR_INVALID for nrhs < 1 or precision FP64. */
+nmg_status nmg_solve_many(nmg_hierarchy* h, int nrhs, const double* b, double* x, const nmg_solve_opts* opts,
+                          nmg_solve_info* info);
+
 /* ---- serving: many solves of problem (1), one per Newton step of different
  * simulations (Section 4.2, Eq. (newton): every Newton step solves one linear
  * problem), batched continuously on resident hierarchies.
@@ -228,6 +247,15 @@ nmg_status nmg_coarse_solve(nmg_hierarchy* h, int precision, const void* b, void
 /* z = one V(nu1, nu2)-cycle applied to r on the finest level, zero initial guess
  * on every level (Section 4.3 (II)). */
 nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* r, void* z);
+
+/* z_k = one V(nu1, nu2)-cycle applied to r_k, k = 0..nrhs-1 (float vectors of
+ * ncomp * nodes entries, column k at offset k * ncomp * nodes, device memory),
+ * in groups of up to 8 columns that share every read of the level matrices
+ * and patch inverses.  Precision NMG_PREC_FP32 or NMG_PREC_BF16; engine, tail
+ * and tile settings do not apply (use_graph != 0: graph replay).  Each
+ * column equals nmg_vcycle on that column bit for bit.  NMG_ERR_INVALID for
+ * nrhs < 1 or precision FP64. */
+nmg_status nmg_vcycle_many(nmg_hierarchy* h, const nmg_solve_opts* opts, int nrhs, const void* r, void* z);
 
 /* Copies count patch inverses of a level, starting at patch first, to host
  * memory out (count * n_p * n_p doubles, row-major A_i^{-1}, converted from the

@@ -659,6 +659,168 @@ static nmg_status vcycle_any(Hierarchy* h, const nmg_solve_opts& o, const void* 
     return NMG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-vector V-cycles: K = 4 or 8 right-hand sides per pass over the level
+// matrices and patch inverses (precision FP32 or BF16; FP32 vectors,
+// interleaved in the levels' MultiData buffers).  Per column the same
+// kernels' arithmetic as the per-step V-cycle, so each column's result equals
+// a single V-cycle's bit for bit.
+// ---------------------------------------------------------------------------
+static size_t many_level_bytes(const Geom& g, int l, int K, int which) {
+    if (which == 3) return l > 0 ? (size_t)g.patches * g.np * K * sizeof(float) : 0;
+    return (size_t)g.nodes * g.nc * K * sizeof(float);
+}
+
+// Level buffers for K columns (kept, and reused by calls with fewer).
+static nmg_status ensure_many(Hierarchy* h, int K) {
+    if (h->many_k >= K) return NMG_OK;
+    NMG_CK(cudaStreamSynchronize(h->stream));
+    for (int l = 0; l < h->L; ++l) {
+        MultiData& M = h->lev[l].m;
+        float** q[4] = {&M.b, &M.x, &M.r, &M.corr};
+        for (int w = 0; w < 4; ++w) {
+            if (!*q[w]) continue;
+            for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+                if (*it == (void*)*q[w]) { h->allocs.erase(it); break; }
+            cudaFree(*q[w]);
+            h->bytes -= std::max<size_t>(16, many_level_bytes(h->lev[l].g, l, h->many_k, w));
+            *q[w] = nullptr;
+        }
+    }
+    h->many_k = 0;
+    h->many_gen++;
+    for (int l = 0; l < h->L; ++l) {
+        MultiData& M = h->lev[l].m;
+        float** q[4] = {&M.b, &M.x, &M.r, &M.corr};
+        for (int w = 0; w < 4; ++w) NMG_TRY(dalloc(h, (void**)q[w], many_level_bytes(h->lev[l].g, l, K, w)));
+    }
+    h->many_k = K;
+    return NMG_OK;
+}
+
+// False if a level's inverses are not in the layout the streaming apply needs
+// (16-byte aligned, unpadded n_p x n_p columns); never the case for
+// hierarchies built by nmg_create_hierarchy.
+static bool many_layout_ok(const Hierarchy* h, int prec) {
+    const size_t es = store_size(prec);
+    for (int l = 1; l < h->L; ++l) {
+        const PrecData& P = h->lev[l].p[prec];
+        const int64_t np = h->lev[l].g.np;
+        if ((uintptr_t)P.inv % 16 || (P.inv_stride * (int64_t)es) % 16 || P.inv_stride < np * np ||
+            P.inv_stride * (int64_t)es > np * np * (int64_t)es + 16)
+            return false;
+    }
+    return true;
+}
+
+template <int K>
+static void smooth_level_many(Hierarchy* h, int l, int prec, int steps, bool x_zero, float omega, bool average) {
+    Level& L = h->lev[l];
+    MultiData& M = L.m;
+    const Geom& g = L.g;
+    cudaStream_t s = h->stream;
+    if (steps == 0 && x_zero) {
+        cudaMemsetAsync(M.x, 0, g.nodes * g.nc * K * sizeof(float), s);
+        return;
+    }
+    for (int st = 0; st < steps; ++st) {
+        const float* d = M.b;
+        if (!(st == 0 && x_zero)) {
+            launch_spmv_many<K>(g, (const float*)L.p[prec].A, M.x, M.b, M.r, true, s);
+            d = M.r;
+        }
+        if (prec == NMG_PREC_FP32)
+            launch_vanka_apply_many<K, float>(g, (const float*)L.p[prec].inv, L.p[prec].inv_stride, d, M.corr,
+                                              h->flags + FLAG_ABORT, s);
+        else
+            launch_vanka_apply_many<K, __nv_bfloat16>(g, (const __nv_bfloat16*)L.p[prec].inv, L.p[prec].inv_stride,
+                                                      d, M.corr, h->flags + FLAG_ABORT, s);
+        launch_vanka_update_many<K>(g, M.corr, M.x, M.x, st == 0 && x_zero, omega, average, s);
+    }
+}
+
+// One V(nu1, nu2)-cycle on the finest level's multi-vector buffers b -> x,
+// the steps of vcycle_levels without cluster tail or tile fusion.
+template <int K>
+static void vcycle_many_levels(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting) {
+    cudaStream_t s = h->stream;
+    const bool avg = weighting == NMG_WEIGHT_AVERAGE;
+    const float om = (float)omega;
+    const int top = h->L - 1;
+    for (int l = top; l >= 1; --l) {
+        Level& L = h->lev[l];
+        smooth_level_many<K>(h, l, prec, nu1, true, om, avg);
+        launch_spmv_many<K>(L.g, (const float*)L.p[prec].A, L.m.x, L.m.b, L.m.r, true, s);
+        launch_restrict_many<K>(L.g, h->lev[l - 1].g, L.m.r, h->lev[l - 1].m.b, h->lev[l - 1].mask, s);
+    }
+    launch_coarse_gemv_many<K>(h->coarse_inv, h->n0, h->lev[0].m.b, h->lev[0].m.x, s);
+    for (int l = 1; l <= top; ++l) {
+        Level& L = h->lev[l];
+        launch_prolong_add_many<K>(L.g, h->lev[l - 1].g, h->lev[l - 1].m.x, L.m.x, L.mask, s);
+        smooth_level_many<K>(h, l, prec, nu2, false, om, avg);
+    }
+}
+
+// The multi-vector V-cycle on the level buffers: replayed from a graph
+// (captured on first use per precision, K and options) when use_graph, else
+// launched kernel by kernel.
+template <int K>
+static nmg_status run_vcycle_many(Hierarchy* h, const nmg_solve_opts& o) {
+    const int prec = o.precision, ki = K == 4 ? 0 : 1;
+    if (!o.use_graph) {
+        vcycle_many_levels<K>(h, prec, o.nu1, o.nu2, o.omega, o.weighting);
+        return NMG_OK;
+    }
+    const int key[4] = {o.nu1, o.nu2, o.weighting, h->many_gen};
+    cudaGraphExec_t& ex = h->mgraph[prec][ki];
+    if (!ex || std::memcmp(key, h->mgraph_key[prec][ki], sizeof(key)) != 0 || h->mgraph_omega[prec][ki] != o.omega) {
+        if (ex) cudaGraphExecDestroy(ex);
+        ex = nullptr;
+        cudaGraph_t graph;
+        NMG_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t before = g_launches;
+        vcycle_many_levels<K>(h, prec, o.nu1, o.nu2, o.omega, o.weighting);
+        h->mgraph_nodes[prec][ki] = g_launches - before;
+        g_launches = before;
+        NMG_CK(cudaStreamEndCapture(h->stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        NMG_CK(e);
+        std::memcpy(h->mgraph_key[prec][ki], key, sizeof(key));
+        h->mgraph_omega[prec][ki] = o.omega;
+    }
+    NMG_CK(cudaGraphLaunch(ex, h->stream));
+    g_launches += h->mgraph_nodes[prec][ki];
+    return NMG_OK;
+}
+
+// z_k = M^{-1} r_k for ncols <= 8 columns given by pointers (FP32 vectors of
+// the finest level): interleave, one multi-vector V-cycle, de-interleave.
+static nmg_status vcycle_cols(Hierarchy* h, const nmg_solve_opts& o, int ncols, const ColPtrs& in,
+                              const ColPtrsOut& out) {
+    const Level& F = h->lev[h->L - 1];
+    const int64_t n = F.g.nodes * F.g.nc;
+    const int K = ncols <= 4 ? 4 : 8;
+    NMG_TRY(ensure_many(h, K));
+    if (K == 4) {
+        launch_pack<4>(in, ncols, n, F.m.b, h->stream);
+        NMG_TRY(run_vcycle_many<4>(h, o));
+        launch_unpack<4>(F.m.x, out, ncols, n, h->stream);
+    } else {
+        launch_pack<8>(in, ncols, n, F.m.b, h->stream);
+        NMG_TRY(run_vcycle_many<8>(h, o));
+        launch_unpack<8>(F.m.x, out, ncols, n, h->stream);
+    }
+    return NMG_OK;
+}
+
+static nmg_status check_many(Hierarchy* h, const nmg_solve_opts& o) {
+    if (o.precision != NMG_PREC_FP32 && o.precision != NMG_PREC_BF16)
+        return fail(NMG_ERR_INVALID, "multi-vector V-cycles run in precision FP32 or BF16");
+    if (!many_layout_ok(h, o.precision)) return fail(NMG_ERR_INVALID, "patch inverse layout");
+    return NMG_OK;
+}
+
 // z_j = M^{-1} v_j for FP64 vectors v, z on the finest level.
 static nmg_status precondition(Hierarchy* h, const nmg_solve_opts& o, const double* v, double* z) {
     return vcycle_any(h, o, v, z, true);
@@ -691,8 +853,9 @@ static bool is_device_ptr(const void* p) {
 }
 
 struct SolveJob {
-    enum Phase { P_NONE, P_NORM, P_CYCLE, P_ITER, P_FINISH, P_DONE };
+    enum Phase { P_NONE, P_NORM, P_CYCLE, P_ITER, P_FINISH, P_DONE, P_WANT };
     bool loop = false;        // the current cycle's steps were enqueued as one graph loop
+    bool grouped = false;     // one column of a multi-vector solve: the group enqueues its V-cycles (P_WANT)
     Hierarchy* h = nullptr;
     nmg_solve_opts o{};
     const double* b_user = nullptr;
@@ -754,18 +917,28 @@ static void job_enqueue_cycle(SolveJob& J) {
 // cycle goes on.  in_loop: the launches are being captured as the body of a
 // graph loop whose condition the decision sets (the V-cycle is captured
 // inline then).
+static void enqueue_arnoldi(Hierarchy* h, const nmg_solve_opts& o, bool in_loop, cudaGraphConditionalHandle loop);
+
 static nmg_status enqueue_step(Hierarchy* h, const nmg_solve_opts& o, int engine, bool in_loop,
                                cudaGraphConditionalHandle loop) {
-    const Geom& g = h->lev[h->L - 1].g;
-    const int64_t n = g.nodes * g.nc;
-    const int m = o.restart;
-    cudaStream_t s = h->stream;
     if (in_loop) {
         h->fused[o.precision] = engine == NMG_ENGINE_FUSED;
         vcycle_dispatch(h, o.precision, o, nullptr, nullptr);
     } else {
         NMG_TRY(vcycle_in_place(h, o));
     }
+    enqueue_arnoldi(h, o, in_loop, loop);
+    return NMG_OK;
+}
+
+// The part of an FGMRES step after z_j = M^{-1} v_j (z_j in the finest
+// level's V-cycle result buffer of the precision): product, Gram-Schmidt,
+// norm, Givens update, scaling into the next V-cycle input and decision.
+static void enqueue_arnoldi(Hierarchy* h, const nmg_solve_opts& o, bool in_loop, cudaGraphConditionalHandle loop) {
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    const int m = o.restart;
+    cudaStream_t s = h->stream;
     const PrecData& PF = h->lev[h->L - 1].p[o.precision];
     double* A64 = h->lev[h->L - 1].A64;
     if (o.precision == NMG_PREC_FP64)
@@ -781,7 +954,6 @@ static nmg_status enqueue_step(Hierarchy* h, const nmg_solve_opts& o, int engine
     else
         launch_gs_update_scale<float>(h->V, n, h->cyc, h->scal, h->w64, (float*)F.p[o.precision].b, n, s);
     launch_decide(h->scal, h->cyc, o.rtol, o.maxit, m, loop, in_loop, s);
-    return NMG_OK;
 }
 
 // The steps of one restart cycle as one executable graph: a while-loop node
@@ -858,6 +1030,10 @@ static cudaGraphExec_t cycle_graph(Hierarchy* h, const nmg_solve_opts& o, int en
 static void job_enqueue_iter(SolveJob& J) {
     Hierarchy* h = J.h;
     cudaStream_t s = h->stream;
+    if (J.grouped) {   // the next step waits for the group's multi-vector V-cycle
+        J.phase = SolveJob::P_WANT;
+        return;
+    }
     cudaGraphExec_t loop = J.o.use_graph == 2 ? cycle_graph(h, J.o, J.engine) : nullptr;
     J.loop = loop != nullptr;
     if (loop) {
@@ -1054,9 +1230,17 @@ nmg_status nmg_default_opts(nmg_solve_opts* o) {
 }
 
 static void free_all(Hierarchy* h) {
+    for (Hierarchy* c : h->many_ws) {
+        cudaStreamSynchronize(c->stream);
+        free_all(c);
+        delete c;
+    }
+    h->many_ws.clear();
     for (int p = 0; p < 3; ++p) {
         if (h->vgraph[p]) cudaGraphExecDestroy(h->vgraph[p]);
         if (h->cgraph[p]) cudaGraphExecDestroy(h->cgraph[p]);
+        for (int k = 0; k < 2; ++k)
+            if (h->mgraph[p][k]) cudaGraphExecDestroy(h->mgraph[p][k]);
     }
     for (void* a : h->allocs) cudaFree(a);
     h->allocs.clear();
@@ -1173,6 +1357,117 @@ static nmg_status clone_workspace(Hierarchy* base, size_t budget, Hierarchy** ou
     return NMG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-vector solves: FGMRES per column, each on its own workspace (column 0
+// on h, the others on workspace clones of h that share its operator), all on
+// h's stream and stepped in lockstep by the host: after each host round the
+// columns that wait for a preconditioner application get one multi-vector
+// V-cycle together, then each column's Arnoldi step.  A column's kernels and
+// their order are those of a host-stepped nmg_solve with the per-step
+// V-cycle engine, so each column's solution and iteration count equal a
+// single solve's bit for bit.
+// ---------------------------------------------------------------------------
+static nmg_status many_workspaces(Hierarchy* h, int cols) {
+    while ((int)h->many_ws.size() < cols - 1) {
+        Hierarchy* c = nullptr;
+        NMG_TRY(clone_workspace(h, h->desc.mem_budget_bytes, &c));
+        h->many_ws.push_back(c);
+    }
+    // the operator may have been set again since the clones were made
+    for (Hierarchy* c : h->many_ws) {
+        c->coarse_inv = h->coarse_inv;
+        c->n0 = h->n0;
+        for (int l = 0; l < h->L; ++l) {
+            c->lev[l].ready = h->lev[l].ready;
+            c->lev[l].A64 = h->lev[l].A64;
+            c->lev[l].mask = h->lev[l].mask;
+            for (int p = 0; p < 3; ++p) {
+                c->lev[l].p[p].A = h->lev[l].p[p].A;
+                c->lev[l].p[p].inv = h->lev[l].p[p].inv;
+                c->lev[l].p[p].inv_stride = h->lev[l].p[p].inv_stride;
+            }
+        }
+    }
+    return NMG_OK;
+}
+
+static nmg_status solve_group(Hierarchy* h, int ncols, const double* const* b, double* const* x,
+                              const nmg_solve_opts& o, nmg_solve_info* info) {
+    NMG_TRY(many_workspaces(h, ncols));
+    Hierarchy* ws[kMaxCols];
+    cudaStream_t own[kMaxCols];
+    SolveJob J[kMaxCols];
+    nmg_solve_opts oc = o;
+    oc.engine = NMG_ENGINE_KERNELS;   // the columns' own V-cycles are never launched
+    oc.tail_patches = 0;
+    oc.tile_patches = 0;
+    for (int k = 0; k < ncols; ++k) {
+        ws[k] = k == 0 ? h : h->many_ws[k - 1];
+        own[k] = ws[k]->stream;
+        ws[k]->stream = h->stream;
+    }
+    nmg_status st = NMG_OK;
+    int started = 0;
+    for (; started < ncols; ++started) {
+        st = job_start(J[started], ws[started], b[started], x[started], oc);
+        if (st != NMG_OK) break;
+        J[started].grouped = true;
+    }
+    while (st == NMG_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { st = fail(NMG_ERR_CUDA, std::string("solve: ") + cudaGetErrorString(e)); break; }
+        int want[kMaxCols], nw = 0;
+        bool live = false;
+        for (int k = 0; k < started; ++k) {
+            if (J[k].phase == SolveJob::P_DONE) continue;
+            job_advance(J[k]);
+            if (J[k].phase == SolveJob::P_WANT) want[nw++] = k;
+            live = live || J[k].phase != SolveJob::P_DONE;
+        }
+        if (!live) break;
+        if (nw == 0) continue;
+        ColPtrs in{};
+        ColPtrsOut out{};
+        for (int q = 0; q < nw; ++q) {
+            const PrecData& P = ws[want[q]]->lev[h->L - 1].p[o.precision];
+            in.p[q] = (const float*)P.b;
+            out.p[q] = (float*)P.x;
+        }
+        st = vcycle_cols(h, o, nw, in, out);
+        for (int q = 0; q < nw && st == NMG_OK; ++q) {
+            SolveJob& Jk = J[want[q]];
+            Hierarchy* w = ws[want[q]];
+            enqueue_arnoldi(w, Jk.o, false, 0);
+            cudaMemcpyAsync(w->host_scal, w->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            cudaMemcpyAsync(w->host_cyc, w->cyc, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            Jk.phase = SolveJob::P_ITER;
+        }
+    }
+    // a bounded wait of the multi-vector apply that ran out fails every column
+    int abort_flag = 0;
+    cudaStreamSynchronize(h->stream);
+    if (cudaMemcpy(&abort_flag, h->flags + FLAG_ABORT, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+        abort_flag) {
+        cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int));
+        fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
+        for (int k = 0; k < started; ++k) job_fail(J[k], NMG_ERR_TIMEOUT);
+    }
+    for (int k = 0; k < ncols; ++k) ws[k]->stream = own[k];
+    nmg_status first = st;
+    for (int k = 0; k < ncols; ++k) {
+        if (k >= started || st != NMG_OK) {
+            J[k].st = st != NMG_OK ? st : NMG_ERR_INVALID;
+            J[k].phase = SolveJob::P_DONE;
+        }
+        if (first == NMG_OK && J[k].st != NMG_OK) {
+            first = J[k].st;
+            g_last_error = J[k].err;
+        }
+        job_info(J[k], info ? info + k : nullptr);
+    }
+    return first;
+}
+
 nmg_status nmg_create_hierarchy(const nmg_mesh_desc* d, nmg_hierarchy** out) {
     if (!d || !out) return fail(NMG_ERR_INVALID, "NULL argument");
     *out = nullptr;
@@ -1261,6 +1556,7 @@ nmg_status nmg_destroy_hierarchy(nmg_hierarchy* h) {
 nmg_status nmg_hierarchy_bytes(nmg_hierarchy* h, size_t* bytes) {
     if (!h || !bytes) return fail(NMG_ERR_INVALID, "NULL argument");
     *bytes = h->bytes;
+    for (const Hierarchy* c : h->many_ws) *bytes += c->bytes;
     return NMG_OK;
 }
 
@@ -1432,6 +1728,64 @@ nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* 
         return fail(NMG_ERR_TIMEOUT, "the persistent V-cycle aborted (grid barrier or copy wait ran out)");
     }
     return NMG_OK;
+}
+
+nmg_status nmg_vcycle_many(nmg_hierarchy* h, const nmg_solve_opts* opts, int nrhs, const void* r, void* z) {
+    if (!h || !r || !z || nrhs < 1) return fail(NMG_ERR_INVALID, "NULL argument or nrhs < 1");
+    NMG_TRY(validate_opts(opts));
+    NMG_TRY(check_ready(h, opts->precision));
+    NMG_TRY(check_many(h, *opts));
+    enter(h);
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
+        const int nc = std::min(kMaxCols, nrhs - c0);
+        ColPtrs in{};
+        ColPtrsOut out{};
+        for (int k = 0; k < nc; ++k) {
+            in.p[k] = (const float*)r + (int64_t)(c0 + k) * n;
+            out.p[k] = (float*)z + (int64_t)(c0 + k) * n;
+        }
+        NMG_TRY(vcycle_cols(h, *opts, nc, in, out));
+    }
+    NMG_TRY(finish_op(h));
+    int f[FLAG_COUNT];
+    NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f[FLAG_ABORT]) {
+        cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int));
+        return fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
+    }
+    return NMG_OK;
+}
+
+nmg_status nmg_solve_many(nmg_hierarchy* h, int nrhs, const double* b, double* x, const nmg_solve_opts* opts,
+                          nmg_solve_info* info) {
+    if (!h || !b || !x || nrhs < 1) return fail(NMG_ERR_INVALID, "NULL argument or nrhs < 1");
+    NMG_TRY(validate_opts(opts));
+    NMG_TRY(check_ready(h, opts->precision));
+    NMG_TRY(check_many(h, *opts));
+    enter(h);
+    const Geom& g = h->lev[h->L - 1].g;
+    const int64_t n = g.nodes * g.nc;
+    nmg_status first = NMG_OK;
+    std::string err;
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
+        const int nc = std::min(kMaxCols, nrhs - c0);
+        const double* bp[kMaxCols];
+        double* xp[kMaxCols];
+        for (int k = 0; k < nc; ++k) {
+            bp[k] = b + (int64_t)(c0 + k) * n;
+            xp[k] = x + (int64_t)(c0 + k) * n;
+        }
+        const nmg_status st = solve_group(h, nc, bp, xp, *opts, info ? info + c0 : nullptr);
+        if (st != NMG_OK && first == NMG_OK) {
+            first = st;
+            err = g_last_error;
+        }
+        if (st == NMG_ERR_CUDA || st == NMG_ERR_OOM) break;
+    }
+    if (first != NMG_OK) g_last_error = err;
+    return first;
 }
 
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int prec, int64_t first, int64_t count, double* out) {

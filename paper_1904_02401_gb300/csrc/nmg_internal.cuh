@@ -54,12 +54,22 @@ struct PrecData {                 // per-precision data of one level
     void* corr2 = nullptr;        // second correction buffer of the tile-fused steps (ping-pong with corr)
 };
 
+// Multi-vector V-cycle buffers of one level (FP32, K columns interleaved:
+// value (u, k) at u * K + k), allocated on the first multi-vector call.
+struct MultiData {
+    float* b = nullptr;
+    float* x = nullptr;
+    float* r = nullptr;
+    float* corr = nullptr;        // patches * n_p * K
+};
+
 struct Level {
     Geom g;
     bool ready = false;
     double* A64 = nullptr;        // FP64 stencil matrix (always kept: outer FGMRES + FP64 mode)
     uint8_t* mask = nullptr;      // Dirichlet flag per unknown
     PrecData p[3];                // NMG_PREC_FP64 / FP32 / BF16
+    MultiData m;
 };
 
 struct Hierarchy {
@@ -124,6 +134,15 @@ struct Hierarchy {
     struct Trial { int engine, tail, fused, tile; double us; };
     std::vector<Trial> tuning[3];          // the autotuner's measurements, per precision
     double prof_bytes = 0.0;
+    // multi-vector V-cycles: columns the level buffers hold (0: none yet), and a
+    // graph per (precision, K = 4 / 8) keyed by nu1, nu2, weighting and omega
+    int many_k = 0;
+    int many_gen = 0;
+    cudaGraphExec_t mgraph[3][2] = {};
+    int mgraph_key[3][2][4] = {};
+    double mgraph_omega[3][2] = {};
+    int64_t mgraph_nodes[3][2] = {};
+    std::vector<Hierarchy*> many_ws;     // workspaces of columns 1.. of multi-vector solves (share the operator)
     std::vector<void*> allocs;
 };
 
@@ -185,6 +204,37 @@ template <typename T>
 void launch_coarse_gemv(const double* inv, int64_t n, const T* b, T* x, cudaStream_t s);
 template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Multi-vector V-cycle launchers (multi_kernels.cu): K = 4 or 8 interleaved
+// FP32 columns; per column the arithmetic of the single-vector launchers.
+// ---------------------------------------------------------------------------
+constexpr int kMaxCols = 8;
+struct ColPtrs { const float* p[kMaxCols]; };
+struct ColPtrsOut { float* p[kMaxCols]; };
+template <int K>
+void launch_spmv_many(const Geom& g, const float* A, const float* x, const float* b, float* y, bool residual,
+                      cudaStream_t s);
+// false (nothing launched) if the inverses are not in the unpadded 16-byte
+// aligned column layout the bulk copies need
+template <int K, typename TS>
+bool launch_vanka_apply_many(const Geom& g, const TS* inv, int64_t stride, const float* d, float* corr, int* flag,
+                             cudaStream_t s);
+template <int K>
+void launch_vanka_update_many(const Geom& g, const float* corr, const float* x_in, float* x_out, bool x_zero,
+                              float omega, bool average, cudaStream_t s);
+template <int K>
+void launch_restrict_many(const Geom& f, const Geom& c, const float* rf, float* rc, const uint8_t* cmask,
+                          cudaStream_t s);
+template <int K>
+void launch_prolong_add_many(const Geom& f, const Geom& c, const float* ec, float* xf, const uint8_t* fmask,
+                             cudaStream_t s);
+template <int K>
+void launch_coarse_gemv_many(const double* inv, int64_t n, const float* b, float* x, cudaStream_t s);
+template <int K>
+void launch_pack(const ColPtrs& src, int ncols, int64_t n, float* out, cudaStream_t s);
+template <int K>
+void launch_unpack(const float* in, const ColPtrsOut& dst, int ncols, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Tile-fused smoothing steps (tile_kernels.cu): one CTA per tile of patches

@@ -107,6 +107,8 @@ _SIGS = {
     "nmg_prolongate_add": [_H, C.c_int, C.c_int, _P, _P],
     "nmg_coarse_solve": [_H, C.c_int, _P, _P],
     "nmg_vcycle": [_H, C.POINTER(nmg_solve_opts), _P, _P],
+    "nmg_vcycle_many": [_H, C.POINTER(nmg_solve_opts), C.c_int, _P, _P],
+    "nmg_solve_many": [_H, C.c_int, _P, _P, C.POINTER(nmg_solve_opts), _P],
     "nmg_get_patch_inverses": [_H, C.c_int, C.c_int, C.c_int64, C.c_int64, _P],
     "nmg_hierarchy_bytes": [_H, C.POINTER(C.c_size_t)],
     "nmg_destroy_hierarchy": [_H],
@@ -196,6 +198,15 @@ def nmg_coarse_solve(h, precision, b, x) -> int:
 
 def nmg_vcycle(h, opts: nmg_solve_opts, r, z) -> int:
     return _lib.nmg_vcycle(h, C.byref(opts), ptr(r), ptr(z))
+
+
+def nmg_vcycle_many(h, opts: nmg_solve_opts, nrhs, r, z) -> int:
+    return _lib.nmg_vcycle_many(h, C.byref(opts), nrhs, ptr(r), ptr(z))
+
+
+def nmg_solve_many(h, nrhs, b, x, opts: nmg_solve_opts, info=None) -> int:
+    """info: None or a ctypes array of nrhs nmg_solve_info records."""
+    return _lib.nmg_solve_many(h, nrhs, ptr(b), ptr(x), C.byref(opts), C.cast(info, C.c_void_p) if info is not None else None)
 
 
 def nmg_get_patch_inverses(h, level, precision, first, count, out) -> int:

@@ -65,6 +65,15 @@ class Session:
             nmg.check(st)
         return info
 
+    def solve_many(self, b, x, nrhs, **opts):
+        """nrhs columns (column k at offset k * unknowns of b and x); returns the
+        list of per-column nmg_solve_info records."""
+        infos = (nmg.nmg_solve_info * nrhs)()
+        st = nmg.nmg_solve_many(self.handle, nrhs, b, x, solve_opts(**opts), infos)
+        if st < 0 and st != nmg.NMG_ERR_NOT_CONVERGED:
+            nmg.check(st)
+        return list(infos)
+
     def bytes(self) -> int:
         v = C.c_size_t()
         nmg.check(nmg.nmg_hierarchy_bytes(self.handle, v))
