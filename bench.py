@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--mesh", default=None,
                     help="serving: one mesh only, e.g. 2d:128 or 3d:32 (many right-hand sides on one hierarchy)")
+    ap.add_argument("--rhs", type=int, default=8,
+                    help="columns of the multi-right-hand-side measurement (nmg_solve_many); 0 skips it")
     ap.add_argument("--workspaces", type=int, default=0,
                     help="serving: extra concurrent requests per hierarchy (nmg_server_set_workspaces)")
     ap.add_argument("--profile-range", action="store_true",
@@ -364,6 +366,8 @@ def gpu_arm(args):
         set_ms.append(1000.0 * (time.perf_counter() - t))
     del rp_d, ci_d, v_d
 
+    multi = _multi_rhs(args, S, sysm, stream, flush, use_graph) if args.rhs > 0 and args.precision != 0 else None
+
     ms = statistics.mean(times)
     ms_max, wall_max = max_over_ranks([ms, wall], dist, "cuda")
 
@@ -421,6 +425,7 @@ def gpu_arm(args):
                    "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
                    "engine": {1: "per-step kernels", 2: "persistent kernel",
                               3: "per-step kernels, fused update/prolongation + residual"}.get(infos[-1].engine)},
+        "multi_rhs": multi,
         "autotune": json.loads(rep.value.decode()),
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
@@ -441,6 +446,76 @@ def gpu_arm(args):
     S.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _multi_rhs(args, S, sysm, stream, flush, use_graph):
+    """Many right-hand sides against the same hierarchy: K columns (the
+    workload's own right-hand side, then seeded uniform vectors with the
+    Dirichlet entries zero) solved by nmg_solve_many, against the same K
+    columns solved one by one with nmg_solve in the timed configuration; and
+    the multi-vector V-cycle against the single V-cycle per column."""
+    import numpy as np
+    import torch
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+
+    K, prec = args.rhs, args.precision
+    rng = np.random.default_rng(2024)
+    mask = np.asarray(sysm.dirichlet, dtype=bool).reshape(-1)
+    cols = [sysm.rhs]
+    for _ in range(1, K):
+        v = rng.uniform(-1.0, 1.0, sysm.rhs.size)
+        v[mask] = 0.0
+        cols.append(v)
+    B = torch.from_numpy(np.stack(cols)).cuda()
+    X = torch.zeros_like(B)
+    x1 = torch.empty_like(B[0])
+
+    def timed(fn, reps):
+        out = []
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = fn()
+                e1.record(stream)
+                e1.synchronize()
+                out.append((e0.elapsed_time(e1), r))
+        return out
+
+    many = lambda: S.solve_many(B, X, K, precision=prec, use_graph=1)
+    timed(many, 2)
+    runs = timed(many, max(3, args.steps // 2))
+    ms_many = statistics.mean(t for t, _ in runs)
+    infos = runs[-1][1]
+
+    def singles():
+        its = []
+        for k in range(K):
+            its.append(S.solve(B[k], x1, precision=prec, use_graph=use_graph).iterations)
+        return its
+    timed(singles, 1)
+    sruns = timed(singles, 3)
+    ms_single = statistics.mean(t for t, _ in sruns)
+
+    R = B.to(torch.float32)
+    Z = torch.zeros_like(R)
+    o = solve_opts(precision=prec, use_graph=1)
+    vm = lambda: nmg.check(nmg.nmg_vcycle_many(S.handle, o, K, R, Z))
+    timed(vm, 2)
+    v_many = statistics.mean(t for t, _ in timed(vm, 10))
+    z1 = torch.zeros_like(R[0])
+    vs = lambda: nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=1), R[0], z1))
+    timed(vs, 2)
+    v_single = statistics.mean(t for t, _ in timed(vs, 10))
+    return {"what": f"{K} right-hand sides, one hierarchy: nmg_solve_many (lockstep FGMRES, one multi-vector "
+                    f"V-cycle per step for all columns) vs {K} nmg_solve calls; L2 flushed before each timed call",
+            "columns": K, "ms": ms_many, "ms_per_column": ms_many / K, "solves_per_s": 1000.0 * K / ms_many,
+            "single_ms_per_column": ms_single / K, "speedup": ms_single / ms_many,
+            "iterations": [i.iterations for i in infos], "single_iterations": sruns[-1][1],
+            "vcycle_ms_per_column": v_many / K, "single_vcycle_ms": v_single, "vcycle_speedup": v_single * K / v_many}
 
 
 def _spmv_line(prof, hbm, steps):

@@ -46,45 +46,86 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
 }
 
-// y = A X or y = B - A X for K columns, one thread per node (stencil layout of
-// A as in k_spmv).  Per column and row: stencil positions ascending, block
-// columns ascending, one fma per term, as spmv_node / spmv_row.
-template <int DIM, int NC, int K>
-__global__ void __launch_bounds__(256)
-k_spmv_many(Geom g, const float* __restrict__ A, const float* __restrict__ x, const float* __restrict__ b,
-            float* __restrict__ y, bool residual) {
-    NMG_PDL_ENTRY();
+// y = A X or y = B - A X for K columns (stencil layout of A as in k_spmv),
+// one thread per node, with X staged in shared memory: a CTA owns a TX x TY
+// (x TZ) tile of nodes and first copies the K-column values of the tile and
+// its one-node halo (coalesced 16-byte loads), so each node's values cross
+// from L2 about once per tile instead of once per neighbour.  A node's K
+// interleaved columns are 12-32 floats, so one thread per node reading them
+// directly from global memory touches a different 128-byte line per lane;
+// from the padded shared-memory slots the reads are conflict-free.  A is read
+// with a warp covering rows of TX consecutive nodes, the blocks of three
+// stencil positions (one x-row of neighbours) loaded together (every
+// position's block exists in the stencil layout, zero outside the mesh).  Per
+// column and row: stencil positions ascending, block columns ascending, one
+// fma per term, as spmv_node / spmv_row.
+template <int DIM, int NC, int K, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ)
+k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ x, const float* __restrict__ b,
+                 float* __restrict__ y, bool residual) {
     constexpr int NB = NC * NC;
     constexpr int NST = DIM == 2 ? 9 : 27;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= g.nodes) return;
-    int ix, iy, iz;
-    node_xyz(g, i, ix, iy, iz);
-    const int64_t sy = g.nn[0], sz = (int64_t)g.nn[0] * g.nn[1];
+    constexpr int HX = TX + 2, HY = TY + 2, HZ = DIM == 3 ? TZ + 2 : 1;
+    constexpr int NV = NC * K;      // floats per node
+    constexpr int NQ = NV / 4;      // float4 per node
+    // shared-memory slot of a node: an odd number of 16-byte units, so that the
+    // 16-byte reads of 8 consecutive nodes (one phase of a warp's access) fall
+    // in 8 different groups of 4 banks (a slot of 128 bytes would put them all
+    // in the same 4 banks)
+    constexpr int NS = (NQ % 2) ? NV : NV + 4;
+    static_assert(DIM == 3 || TZ == 1, "2d tiles are one node deep");
+    extern __shared__ float4 xs4[];
+    const float* xs = reinterpret_cast<const float*>(xs4);
+    const int tiles_x = (g.nn[0] + TX - 1) / TX, tiles_y = (g.nn[1] + TY - 1) / TY;
+    int blk = blockIdx.x;
+    const int bx = blk % tiles_x;
+    blk /= tiles_x;
+    const int by = blk % tiles_y, bz = blk / tiles_y;
+    const int x0 = bx * TX - 1, y0 = by * TY - 1, z0 = DIM == 3 ? bz * TZ - 1 : 0;
+    NMG_PDL_ENTRY();
+    for (int t = threadIdx.x; t < HX * HY * HZ * NQ; t += TX * TY * TZ) {
+        const int hn = t / NQ, q = t - hn * NQ;
+        const int hx = hn % HX, hy = (hn / HX) % HY, hz = hn / (HX * HY);
+        const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+        if (gx >= 0 && gx < g.nn[0] && gy >= 0 && gy < g.nn[1] && gz >= 0 && gz < g.nn[2])
+            xs4[hn * (NS / 4) + q] = ld4(x + (gx + (int64_t)g.nn[0] * (gy + (int64_t)g.nn[1] * gz)) * NV + 4 * q);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int ix = x0 + 1 + tx, iy = y0 + 1 + ty, iz = DIM == 3 ? z0 + 1 + tz : 0;
+    const int hz0 = DIM == 3 ? tz + 1 : 0;   // the node's own plane in the halo tile
+    if (ix >= g.nn[0] || iy >= g.nn[1] || iz >= g.nn[2]) return;
+    const int64_t i = ix + (int64_t)g.nn[0] * (iy + (int64_t)g.nn[1] * iz);
     float acc[NC][K];
 #pragma unroll
     for (int r = 0; r < NC; ++r)
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
 #pragma unroll
-    for (int s = 0; s < NST; ++s) {
-        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
-        const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
-                        (iz + dz >= 0) && (iz + dz < g.nn[2]);
-        if (ok) {
-            const int64_t j = i + dx + dy * sy + dz * sz;
-            float xv[NC][K];
+    for (int s0 = 0; s0 < NST; s0 += 3) {
+        float av[3][NB];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) ldk<K>(x + (j * NC + c) * K, xv[c]);
-            const float* As = A + (int64_t)s * NB * g.ld + i;
+        for (int q = 0; q < 3; ++q)
 #pragma unroll
-            for (int r = 0; r < NC; ++r)
+            for (int e = 0; e < NB; ++e) av[q][e] = __ldg(A + ((int64_t)(s0 + q) * NB + e) * g.ld + i);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int s = s0 + q;
+            const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+            const bool ok = (ix + dx >= 0) && (ix + dx < g.nn[0]) && (iy + dy >= 0) && (iy + dy < g.nn[1]) &&
+                            (iz + dz >= 0) && (iz + dz < g.nn[2]);
+            if (ok) {
+                const float* xn = xs + ((tx + 1 + dx) + HX * ((ty + 1 + dy) + HY * (hz0 + dz))) * NS;
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const float a = __ldg(As + (int64_t)(r * NC + c) * g.ld);
+                    float xv[K];
+                    ldk<K>(xn + c * K, xv);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[r][k] = fmaf(a, xv[c][k], acc[r][k]);
+                    for (int r = 0; r < NC; ++r)
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[r][k] = fmaf(av[q][r * NC + c], xv[k], acc[r][k]);
                 }
+            }
         }
     }
 #pragma unroll
@@ -474,7 +515,7 @@ void apply_many_dispatch(const Geom& g, const TS* inv, int64_t stride, const flo
         else launch_apply_many<TS, 2, 3, K, F32 ? 6 : 12, 128>(g, inv, stride, d, corr, flag, s);
     } else {
         if (lean) launch_apply_many<TS, 3, 3, K, F32 ? 6 : 12, 96>(g, inv, stride, d, corr, flag, s);
-        else if (F32) launch_apply_many<TS, 3, 4, K, 4, 128>(g, inv, stride, d, corr, flag, s);
+        else if (F32) launch_apply_many<TS, 3, 4, K, 2, 256>(g, inv, stride, d, corr, flag, s);
         else launch_apply_many<TS, 3, 4, K, 4, 256>(g, inv, stride, d, corr, flag, s);
     }
 }
@@ -496,11 +537,32 @@ void apply_many_dispatch(const Geom& g, const TS* inv, int64_t stride, const flo
         }                                                                \
     } while (0)
 
+template <int DIM, int NC, int K, int TX, int TY, int TZ>
+static void launch_spmv_many_tile(const Geom& g, const float* A, const float* x, const float* b, float* y,
+                                  bool residual, cudaStream_t s) {
+    constexpr int NV = NC * K, NS = ((NV / 4) % 2) ? NV : NV + 4;
+    const size_t smem = (size_t)(TX + 2) * (TY + 2) * (DIM == 3 ? TZ + 2 : 1) * NS * sizeof(float);
+    auto kern = k_spmv_many_tile<DIM, NC, K, TX, TY, TZ>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const unsigned tiles = (unsigned)(((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY) *
+                                      (DIM == 3 ? (g.nn[2] + TZ - 1) / TZ : 1));
+    pdl_launch(kern, dim3(tiles), dim3(TX * TY * TZ), smem, s, g, A, x, b, y, residual);
+}
+
+// Tiles of 128 threads: 3d 16 x 4 x 2 nodes (about 150 registers, three CTAs
+// per SM; a warp's matrix loads cover two 64-byte row segments), 2d 32 x 4
+// nodes.
 template <int K>
 void launch_spmv_many(const Geom& g, const float* A, const float* x, const float* b, float* y, bool residual,
                       cudaStream_t s) {
     g_launches += 1;
-    NMG_MANY_DISPATCH(g, K, k_spmv_many, dim3(blocks_for(g.nodes, 256)), dim3(256), 0, s, g, A, x, b, y, residual);
+    if (g.dim == 3) {
+        if (g.nc == 3) launch_spmv_many_tile<3, 3, K, 16, 4, 2>(g, A, x, b, y, residual, s);
+        else launch_spmv_many_tile<3, 4, K, 16, 4, 2>(g, A, x, b, y, residual, s);
+    } else {
+        if (g.nc == 2) launch_spmv_many_tile<2, 2, K, 32, 4, 1>(g, A, x, b, y, residual, s);
+        else launch_spmv_many_tile<2, 3, K, 32, 4, 1>(g, A, x, b, y, residual, s);
+    }
 }
 
 template <int K, typename TS>
