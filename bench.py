@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--profile-range", action="store_true",
                     help="after the warm-up, run one solve between cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off) and exit")
+    ap.add_argument("--profile-many", action="store_true",
+                    help="run one 8-column multi-vector V-cycle and one single V-cycle (plain launches) between "
+                         "cudaProfilerStart and cudaProfilerStop, then exit (for an ncu launch list)")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS),
                     help="cfg2 is the measured workload; the others are for investigation")
     return ap.parse_args()
@@ -300,6 +303,26 @@ def gpu_arm(args):
             nmg.check(nmg.nmg_profile_enable(S.handle, 0))
             prof = (ms.value, cnt.value, bpl.value)
         return times, infos, prof
+
+    if args.profile_many:
+        K = 8
+        R = torch.from_numpy(np.tile(sysm.rhs.astype(np.float32), (K, 1))).cuda()
+        Z = torch.zeros_like(R)
+        z1 = torch.zeros_like(R[0])
+        om = solve_opts(precision=args.precision, use_graph=0)
+        o1 = solve_opts(precision=args.precision, use_graph=0, engine=nmg.NMG_ENGINE_KERNELS)
+        for _ in range(max(1, args.warmup)):
+            nmg.check(nmg.nmg_vcycle_many(S.handle, om, K, R, Z))
+            nmg.check(nmg.nmg_vcycle(S.handle, o1, R[0], z1))
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        nmg.check(nmg.nmg_vcycle_many(S.handle, om, K, R, Z))
+        nmg.check(nmg.nmg_vcycle(S.handle, o1, R[0], z1))
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        if rank == 0:
+            print(json.dumps({"profile_many": WORKLOAD, "columns": K}), flush=True)
+        return
 
     # warm-up (also captures the V-cycle graphs)
     timed_solves(args.precision, args.warmup, use_graph)
