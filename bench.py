@@ -91,6 +91,8 @@ def parse():
                     help="serving: one mesh only, e.g. 2d:128 or 3d:32 (many right-hand sides on one hierarchy)")
     ap.add_argument("--rhs", type=int, default=8,
                     help="columns of the multi-right-hand-side measurement (nmg_solve_many); 0 skips it")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="serving: requests on one hierarchy run as columns of a multi-vector solve (up to 8)")
     ap.add_argument("--workspaces", type=int, default=0,
                     help="serving: extra concurrent requests per hierarchy (nmg_server_set_workspaces)")
     ap.add_argument("--profile-range", action="store_true",
@@ -648,6 +650,7 @@ def serving_arm(args):
     server = C.c_void_p()
     nmg.check(nmg.nmg_server_create(budget, 16, server))
     nmg.check(nmg.nmg_server_set_workspaces(server, args.workspaces))
+    nmg.check(nmg.nmg_server_set_batching(server, args.batch))
 
     def run(reqs, rate):
         tickets = []
@@ -691,6 +694,7 @@ def serving_arm(args):
                                 "hierarchy (right-hand sides seeded per request), FP32 V-cycle / FP64 FGMRES(30), "
                                 "rtol 1e-8, memory budget 150 GB, 16 slots"),
                    "extra_workspaces_per_hierarchy": args.workspaces,
+                   "batched_columns": args.batch,
                    "arrival_rate_per_s": rate, "saturated_solves_per_s": saturated},
         "p50_ms": statistics.median(lat), "p99_ms": lat_sorted[max(0, int(0.99 * len(lat)) - 1)],
         "solves_per_s": len(reqs) / wall, "failed": bad, "mean_iterations": statistics.mean(its),

@@ -210,6 +210,17 @@ nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server*
  * workspace; one is made only when the budget holds it.  NMG_ERR_INVALID for a
  * count outside 0..1024. */
 nmg_status nmg_server_set_workspaces(nmg_server* s, int extra_per_hierarchy);
+/* Serves requests on the same hierarchy as the columns of one multi-vector
+ * solve (see nmg_solve_many): with max_columns > 1, a request whose precision
+ * is NMG_PREC_FP32 or NMG_PREC_BF16 joins its hierarchy's column group when a
+ * column is free and its V-cycle options (precision, nu1, nu2, omega,
+ * weighting) equal the group's, at any point of the others' iterations; every
+ * V-cycle then serves all columns that need one.  Columns finish
+ * independently.  Results equal nmg_solve's bit for bit.  FP64 requests run
+ * alone on their hierarchy when no group runs on it.  The column workspaces
+ * are the hierarchy's own (nmg_solve_many's) and are counted by the budget.
+ * 0 or 1 turns batching off (the default); NMG_ERR_INVALID outside 0..8. */
+nmg_status nmg_server_set_batching(nmg_server* s, int max_columns);
 nmg_status nmg_submit(nmg_server* s, nmg_hierarchy* h, const double* b, double* x,
                       const nmg_solve_opts* opts, uint64_t* ticket);
 nmg_status nmg_poll(nmg_server* s, uint64_t ticket, int timeout_ms, nmg_solve_info* info);

@@ -1905,10 +1905,15 @@ nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launche
 
 namespace nmg {
 
+struct Group;
+
 struct Request {
     uint64_t ticket = 0;
     Hierarchy* h = nullptr;       // the hierarchy the request was submitted on
     Hierarchy* slot = nullptr;    // where it runs: h itself or a workspace clone of h
+    Group* group = nullptr;       // the column group it runs in (batching), else null
+    int col = -1;                 // its column in the group
+    cudaStream_t own_stream = nullptr;   // the column workspace's own stream, restored when it leaves
     const double* b = nullptr;
     double* x = nullptr;
     nmg_solve_opts o{};
@@ -1918,6 +1923,21 @@ struct Request {
     nmg_solve_info info{};
     std::string err;
     std::chrono::steady_clock::time_point t_submit;
+};
+
+// Requests on one hierarchy batched as the columns of a multi-vector solve
+// (nmg_server_set_batching): column k runs on workspace k (the hierarchy, or
+// its k-th column workspace), all on the hierarchy's stream; one event covers
+// the group's enqueued work, and each time it completes the worker advances
+// every column, runs one multi-vector V-cycle for the columns that need one
+// and then their Arnoldi steps.  Columns join and leave at any round.
+struct Group {
+    Hierarchy* h = nullptr;
+    Request* col[kMaxCols] = {};
+    int n = 0;                    // occupied columns
+    nmg_solve_opts vo{};          // the V-cycle options its columns share
+    cudaEvent_t ev = nullptr;
+    bool inflight = false;        // work enqueued since the last round
 };
 
 struct Server {
@@ -1936,7 +1956,16 @@ struct Server {
     std::unordered_map<Hierarchy*, std::vector<Hierarchy*>> clones;
     size_t clone_bytes = 0;
     int extra_workspaces = 0;
+    int batch_columns = 0;        // > 1: FP32 / BF16 requests on one hierarchy run as a column group
+    std::unordered_map<Hierarchy*, Group*> groups;
 };
+
+static bool same_vcycle(const nmg_solve_opts& a, const nmg_solve_opts& b) {
+    return a.precision == b.precision && a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.omega == b.omega &&
+           a.weighting == b.weighting;
+}
+
+static Hierarchy* column_workspace(Hierarchy* h, int k) { return k == 0 ? h : h->many_ws[k - 1]; }
 
 // Memory the running requests hold: each hierarchy with a running request
 // once (its operator and first workspace), plus every workspace clone.
@@ -1970,6 +1999,75 @@ static void finish_request(Server* S, Request* r, std::vector<Request*>& active,
     S->cv_done.notify_all();
 }
 
+static void finish_grouped(Server* S, Request* r, std::vector<Request*>& active, Residency& res) {
+    Group* G = r->group;
+    job_info(r->job, &r->info);
+    r->info.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count();
+    r->err = r->job.err;
+    if (r->col > 0) r->slot->stream = r->own_stream;
+    G->col[r->col] = nullptr;
+    G->n--;
+    res.remove(r->h);
+    active.erase(std::find(active.begin(), active.end(), r));
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->done = true;
+    S->cv_done.notify_all();
+}
+
+// One round of a column group whose enqueued work has completed (q: the
+// event's status): advance every column, retire the finished ones, then one
+// multi-vector V-cycle for the columns that need one and their Arnoldi steps.
+static void advance_group(Server* S, Group* G, cudaError_t q, std::vector<Request*>& active, Residency& res) {
+    Hierarchy* h = G->h;
+    G->inflight = false;
+    int want[kMaxCols], nw = 0;
+    for (int k = 0; k < kMaxCols; ++k) {
+        Request* r = G->col[k];
+        if (!r || r->job.phase == SolveJob::P_DONE) continue;
+        if (q != cudaSuccess) {
+            fail(NMG_ERR_CUDA, std::string("request failed: ") + cudaGetErrorString(q));
+            job_fail(r->job, NMG_ERR_CUDA);
+            r->job.phase = SolveJob::P_DONE;
+            continue;
+        }
+        const int64_t l0 = g_launches;
+        job_advance(r->job);
+        r->job.launches += g_launches - l0;
+        if (r->job.phase == SolveJob::P_WANT) want[nw++] = k;
+    }
+    for (int k = 0; k < kMaxCols; ++k)
+        if (G->col[k] && G->col[k]->job.phase == SolveJob::P_DONE) finish_grouped(S, G->col[k], active, res);
+    if (nw > 0) {
+        ColPtrs in{};
+        ColPtrsOut out{};
+        for (int i = 0; i < nw; ++i) {
+            const PrecData& P = G->col[want[i]]->slot->lev[h->L - 1].p[G->vo.precision];
+            in.p[i] = (const float*)P.b;
+            out.p[i] = (float*)P.x;
+        }
+        const int64_t l0 = g_launches;
+        const nmg_status st = vcycle_cols(h, G->vo, nw, in, out);
+        for (int i = 0; i < nw; ++i) {
+            Request* r = G->col[want[i]];
+            if (st != NMG_OK) {
+                job_fail(r->job, st);
+                job_enqueue_finish(r->job);
+                continue;
+            }
+            Hierarchy* w = r->slot;
+            enqueue_arnoldi(w, r->job.o, false, 0);
+            cudaMemcpyAsync(w->host_scal, w->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            cudaMemcpyAsync(w->host_cyc, w->cyc, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+            r->job.phase = SolveJob::P_ITER;
+            r->job.launches += (g_launches - l0) / nw;
+        }
+    }
+    if (G->n > 0) {
+        cudaEventRecord(G->ev, h->stream);
+        G->inflight = true;
+    }
+}
+
 static void server_loop(Server* S) {
     cudaSetDevice(S->device);
     std::vector<Request*> active;
@@ -1989,12 +2087,44 @@ static void server_loop(Server* S) {
             S->clone_bytes = 0;
             for (auto& kv : S->clones)
                 for (Hierarchy* c : kv.second) S->clone_bytes += c->bytes;
+            for (auto& kv : S->groups)
+                for (Hierarchy* c : kv.first->many_ws) S->clone_bytes += c->bytes;
             for (auto it = S->queue.begin(); it != S->queue.end() && (int)(active.size() + admit.size()) < S->max_slots;) {
                 Request* r = *it;
                 const size_t used = res.bytes + S->clone_bytes;
                 const size_t need = res.with(r->h);
-                const bool fits = S->budget == 0 || used + need <= S->budget || (active.empty() && admit.empty());
+                bool fits = S->budget == 0 || used + need <= S->budget || (active.empty() && admit.empty());
                 Hierarchy* slot = nullptr;
+                Group* G = S->groups.count(r->h) ? S->groups[r->h] : nullptr;
+                const bool batch = S->batch_columns > 1 && r->o.precision != NMG_PREC_FP64;
+                if (fits && batch) {
+                    // a column of the hierarchy's group (none runs alone on it)
+                    if (!busy.count(r->h) && (!G || G->n == 0 || (G->n < S->batch_columns && same_vcycle(G->vo, r->o)))) {
+                        int k = -1;
+                        for (int c = 0; c < S->batch_columns && k < 0; ++c)
+                            if (!G || !G->col[c]) k = c;
+                        if (k >= 0 && many_workspaces(r->h, k + 1) == NMG_OK) {
+                            if (!G) {
+                                G = new Group();
+                                G->h = r->h;
+                                S->groups[r->h] = G;
+                            }
+                            if (G->n == 0) G->vo = r->o;
+                            G->col[k] = r;
+                            G->n++;
+                            r->group = G;
+                            r->col = k;
+                            res.add(r->h);
+                            r->slot = column_workspace(r->h, k);
+                            admit.push_back(r);
+                            it = S->queue.erase(it);
+                            continue;
+                        }
+                    }
+                    ++it;
+                    continue;
+                }
+                if (fits && G && G->n > 0) fits = false;   // the hierarchy runs a column group
                 if (fits) {
                     if (!busy.count(r->h)) slot = r->h;
                     for (size_t c = 0; !slot && c < S->clones[r->h].size(); ++c)
@@ -2027,6 +2157,33 @@ static void server_loop(Server* S) {
         }
         for (Request* r : admit) {
             active.push_back(r);
+            if (r->group) {
+                Hierarchy* h = r->group->h;
+                if (r->col > 0) {
+                    r->own_stream = r->slot->stream;
+                    r->slot->stream = h->stream;
+                }
+                nmg_solve_opts oc = r->o;
+                oc.engine = NMG_ENGINE_KERNELS;
+                oc.tail_patches = 0;
+                oc.tile_patches = 0;
+                const int64_t l0 = g_launches;
+                const nmg_status st = job_start(r->job, r->slot, r->b, r->x, oc);
+                if (st != NMG_OK) {
+                    r->job.st = st;
+                    r->job.err = g_last_error;
+                    r->job.phase = SolveJob::P_DONE;
+                }
+                r->job.grouped = true;
+                r->job.launches = g_launches - l0;
+                Group* G = r->group;
+                if (!G->ev && cudaEventCreateWithFlags(&G->ev, cudaEventDisableTiming) != cudaSuccess) G->ev = nullptr;
+                if (G->ev) {
+                    cudaEventRecord(G->ev, h->stream);
+                    G->inflight = true;
+                }
+                continue;
+            }
             const int64_t l0 = g_launches;
             nmg_status st = job_start(r->job, r->slot, r->b, r->x, r->o);
             if (st == NMG_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) == cudaSuccess) {
@@ -2040,8 +2197,17 @@ static void server_loop(Server* S) {
             r->job.launches = g_launches - l0;
         }
         bool progressed = !admit.empty();
+        for (auto& kv : S->groups) {
+            Group* G = kv.second;
+            if (G->n == 0 || !G->inflight) continue;
+            const cudaError_t q = cudaEventQuery(G->ev);
+            if (q == cudaErrorNotReady) continue;
+            progressed = true;
+            advance_group(S, G, q, active, res);
+        }
         for (size_t i = 0; i < active.size();) {
             Request* r = active[i];
+            if (r->group) { ++i; continue; }
             if (r->job.phase != SolveJob::P_DONE) {
                 const cudaError_t q = cudaEventQuery(r->ev);
                 if (q == cudaErrorNotReady) { ++i; continue; }
@@ -2082,6 +2248,14 @@ nmg_status nmg_server_create(size_t mem_budget_bytes, int max_slots, nmg_server*
     cudaGetDevice(&S->device);
     S->worker = std::thread(nmg::server_loop, S);
     *out = reinterpret_cast<nmg_server*>(S);
+    return NMG_OK;
+}
+
+nmg_status nmg_server_set_batching(nmg_server* server, int max_columns) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S || max_columns < 0 || max_columns > kMaxCols) return fail(NMG_ERR_INVALID, "bad server or column count");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->batch_columns = max_columns;
     return NMG_OK;
 }
 
@@ -2152,6 +2326,10 @@ nmg_status nmg_server_destroy(nmg_server* server) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     for (auto& kv : S->by_ticket) delete kv.second;
+    for (auto& kv : S->groups) {
+        if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+        delete kv.second;
+    }
     for (auto& kv : S->clones)
         for (nmg::Hierarchy* c : kv.second) {
             cudaStreamSynchronize(c->stream);

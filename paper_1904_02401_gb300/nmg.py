@@ -120,6 +120,7 @@ _SIGS = {
     "nmg_poll": [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(nmg_solve_info)],
     "nmg_server_destroy": [C.c_void_p],
     "nmg_server_set_workspaces": [C.c_void_p, C.c_int],
+    "nmg_server_set_batching": [C.c_void_p, C.c_int],
     "nmg_vanka_correct_noalloc": [C.c_int, C.POINTER(C.c_int), C.c_int, _P, C.c_int64, _P, _P, C.c_double,
                                   C.c_int, C.c_int, _P],
 }
@@ -254,6 +255,10 @@ def nmg_server_destroy(server) -> int:
 
 def nmg_server_set_workspaces(server, extra_per_hierarchy) -> int:
     return _lib.nmg_server_set_workspaces(server, extra_per_hierarchy)
+
+
+def nmg_server_set_batching(server, max_columns) -> int:
+    return _lib.nmg_server_set_batching(server, max_columns)
 
 
 def nmg_autotune_report(h, buf, length) -> int:

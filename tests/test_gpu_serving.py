@@ -172,3 +172,55 @@ def test_same_hierarchy_requests_overlap(pool):
                 assert info.iterations == alone[i][1]
     finally:
         nmg.nmg_server_destroy(server)
+
+
+def test_batched_columns(pool):
+    """With batching on, FP32 requests on one hierarchy run as the columns of a
+    multi-vector solve (joining while others iterate, leaving when done), FP64
+    requests and requests with other V-cycle options wait for their turn, and
+    every result and iteration count is bitwise the one nmg_solve gives alone."""
+    import time
+
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    picks = [0, 1, 4]
+    reqs = []
+    for i in range(22):
+        m = picks[i % 3]
+        prec = 0 if i % 7 == 3 else 1
+        omega = 0.7 if i % 5 == 4 else 0.8
+        rtol = 1e-6 if i % 4 == 1 else 1e-8
+        reqs.append((m, prec, omega, rtol, 500 + i))
+    alone = []
+    for m, prec, omega, rtol, seed in reqs:
+        s, S = pool[m]
+        b = _rhs(s, seed)
+        x = torch.empty_like(b)
+        info = S.solve(b, x, precision=prec, omega=omega, rtol=rtol, engine=nmg.NMG_ENGINE_KERNELS)
+        assert info.status == 0
+        alone.append((x.clone(), info.iterations))
+    server = C.c_void_p()
+    nmg.check(nmg.nmg_server_create(0, 16, server))
+    assert nmg.nmg_server_set_batching(server, 9) == nmg.NMG_ERR_INVALID
+    nmg.check(nmg.nmg_server_set_batching(server, 8))
+    try:
+        for rnd in range(2):
+            bufs, tickets = [], []
+            for m, prec, omega, rtol, seed in reqs:
+                b = _rhs(pool[m][0], seed)
+                bufs.append((b, torch.zeros_like(b)))
+            torch.cuda.synchronize()
+            for i, ((m, prec, omega, rtol, seed), (b, x)) in enumerate(zip(reqs, bufs)):
+                t = C.c_uint64()
+                nmg.check(nmg.nmg_submit(server, pool[m][1].handle, b, x,
+                                         solve_opts(precision=prec, omega=omega, rtol=rtol), t))
+                tickets.append(t.value)
+                if rnd == 1 and i % 6 == 5:
+                    time.sleep(0.002)   # later requests join groups that are already iterating
+            for i, t in enumerate(tickets):
+                info = nmg.nmg_solve_info()
+                assert nmg.nmg_poll(server, t, 60000, info) == 0, nmg.nmg_last_error()
+                assert info.iterations == alone[i][1], (rnd, i)
+                assert torch.equal(bufs[i][1], alone[i][0]), (rnd, i)
+    finally:
+        nmg.nmg_server_destroy(server)
