@@ -218,8 +218,10 @@ nmg_status nmg_server_set_workspaces(nmg_server* s, int extra_per_hierarchy);
  * V-cycle then serves all columns that need one.  Columns finish
  * independently.  Results equal nmg_solve's bit for bit.  FP64 requests run
  * alone on their hierarchy when no group runs on it.  The column workspaces
- * are the hierarchy's own (nmg_solve_many's) and are counted by the budget.
- * 0 or 1 turns batching off (the default); NMG_ERR_INVALID outside 0..8. */
+ * are the hierarchy's own (nmg_solve_many's) and are counted by the budget
+ * while columns run.  Do not call nmg_solve_many on a hierarchy while the
+ * server may run requests on it.  0 or 1 turns batching off (the default);
+ * NMG_ERR_INVALID outside 0..8. */
 nmg_status nmg_server_set_batching(nmg_server* s, int max_columns);
 nmg_status nmg_submit(nmg_server* s, nmg_hierarchy* h, const double* b, double* x,
                       const nmg_solve_opts* opts, uint64_t* ticket);

@@ -86,7 +86,6 @@ static nmg_status dalloc(Hierarchy* h, void** p, size_t bytes) {
         if (st_ != NMG_OK) return st_; \
     } while (0)
 
-static size_t prec_size(int prec) { return prec == NMG_PREC_FP64 ? sizeof(double) : sizeof(float); }
 static size_t store_size(int prec) {
     return prec == NMG_PREC_FP64 ? sizeof(double) : prec == NMG_PREC_FP32 ? sizeof(float) : sizeof(__nv_bfloat16);
 }
@@ -819,11 +818,6 @@ static nmg_status check_many(Hierarchy* h, const nmg_solve_opts& o) {
         return fail(NMG_ERR_INVALID, "multi-vector V-cycles run in precision FP32 or BF16");
     if (!many_layout_ok(h, o.precision)) return fail(NMG_ERR_INVALID, "patch inverse layout");
     return NMG_OK;
-}
-
-// z_j = M^{-1} v_j for FP64 vectors v, z on the finest level.
-static nmg_status precondition(Hierarchy* h, const nmg_solve_opts& o, const double* v, double* z) {
-    return vcycle_any(h, o, v, z, true);
 }
 
 static nmg_status ensure_krylov(Hierarchy* h, int m) {
@@ -1936,6 +1930,7 @@ struct Group {
     Request* col[kMaxCols] = {};
     int n = 0;                    // occupied columns
     nmg_solve_opts vo{};          // the V-cycle options its columns share
+    size_t ws_bytes = 0;          // bytes of the column workspaces, taken while columns run
     cudaEvent_t ev = nullptr;
     bool inflight = false;        // work enqueued since the last round
 };
@@ -2087,8 +2082,8 @@ static void server_loop(Server* S) {
             S->clone_bytes = 0;
             for (auto& kv : S->clones)
                 for (Hierarchy* c : kv.second) S->clone_bytes += c->bytes;
-            for (auto& kv : S->groups)
-                for (Hierarchy* c : kv.first->many_ws) S->clone_bytes += c->bytes;
+            for (auto& kv : S->groups)   // (a group without columns may outlive its hierarchy)
+                if (kv.second->n > 0) S->clone_bytes += kv.second->ws_bytes;
             for (auto it = S->queue.begin(); it != S->queue.end() && (int)(active.size() + admit.size()) < S->max_slots;) {
                 Request* r = *it;
                 const size_t used = res.bytes + S->clone_bytes;
@@ -2110,6 +2105,8 @@ static void server_loop(Server* S) {
                                 S->groups[r->h] = G;
                             }
                             if (G->n == 0) G->vo = r->o;
+                            G->ws_bytes = 0;
+                            for (Hierarchy* c : r->h->many_ws) G->ws_bytes += c->bytes;
                             G->col[k] = r;
                             G->n++;
                             r->group = G;
