@@ -177,3 +177,41 @@ def test_96cube_solve_residual(big, prec):
     assert _true_rel_residual(s.fine, s.rhs, x.cpu().numpy()) <= 1e-8
     assert abs(info.rel_residual - _true_rel_residual(s.fine, s.rhs, x.cpu().numpy())) < 1e-10
     assert info.iterations <= 60
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_96cube_multi_vector(big, prec):
+    """8 columns through the multi-vector V-cycle (graph replay, as bench.py's
+    multi_rhs times it) equal single V-cycles bit for bit at full size, and a
+    2-column multi-vector solve equals the single solves (counts, iterates)
+    and meets the true FP64 residual."""
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    s, S, stream = big
+    rng = np.random.default_rng(77)
+    mask = s.dirichlet.astype(bool)
+    cols = [s.rhs]
+    for _ in range(7):
+        v = rng.uniform(-1.0, 1.0, s.rhs.size)
+        v[mask] = 0.0
+        cols.append(v)
+    B = torch.from_numpy(np.stack(cols)).cuda()
+    R = B.to(torch.float32)
+    Z = torch.full_like(R, float("nan"))
+    with torch.cuda.stream(stream):
+        nmg.check(nmg.nmg_vcycle_many(S.handle, solve_opts(precision=prec, use_graph=1), 8, R, Z))
+        for k in (0, 3, 7):
+            z = torch.zeros_like(R[k])
+            nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=0, engine=nmg.NMG_ENGINE_KERNELS),
+                                     R[k].contiguous(), z))
+            torch.cuda.synchronize()
+            assert torch.equal(Z[k], z), k
+        X = torch.zeros_like(B[:2])
+        infos = S.solve_many(B[:2].contiguous(), X, 2, precision=prec)
+        for k in range(2):
+            x = torch.empty_like(B[k])
+            info = S.solve(B[k].contiguous(), x, precision=prec, use_graph=0, engine=nmg.NMG_ENGINE_KERNELS)
+            assert infos[k].status == info.status == 0
+            assert infos[k].iterations == info.iterations
+            assert torch.equal(X[k], x)
+            assert _true_rel_residual(s.fine, cols[k], X[k].cpu().numpy()) <= 1e-8
