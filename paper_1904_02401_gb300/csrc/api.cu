@@ -730,10 +730,10 @@ static void smooth_level_many(Hierarchy* h, int l, int prec, int steps, bool x_z
         }
         if (prec == NMG_PREC_FP32)
             launch_vanka_apply_many<K, float>(g, (const float*)L.p[prec].inv, L.p[prec].inv_stride, d, M.corr,
-                                              h->flags + FLAG_ABORT, s);
+                                              h->flags + FLAG_MANY, s);
         else
             launch_vanka_apply_many<K, __nv_bfloat16>(g, (const __nv_bfloat16*)L.p[prec].inv, L.p[prec].inv_stride,
-                                                      d, M.corr, h->flags + FLAG_ABORT, s);
+                                                      d, M.corr, h->flags + FLAG_MANY, s);
         launch_vanka_update_many<K>(g, M.corr, M.x, M.x, st == 0 && x_zero, omega, average, s);
     }
 }
@@ -1440,9 +1440,9 @@ static nmg_status solve_group(Hierarchy* h, int ncols, const double* const* b, d
     // a bounded wait of the multi-vector apply that ran out fails every column
     int abort_flag = 0;
     cudaStreamSynchronize(h->stream);
-    if (cudaMemcpy(&abort_flag, h->flags + FLAG_ABORT, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+    if (cudaMemcpy(&abort_flag, h->flags + FLAG_MANY, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
         abort_flag) {
-        cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int));
+        cudaMemset(h->flags + FLAG_MANY, 0, sizeof(int));
         fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
         for (int k = 0; k < started; ++k) job_fail(J[k], NMG_ERR_TIMEOUT);
     }
@@ -1745,8 +1745,8 @@ nmg_status nmg_vcycle_many(nmg_hierarchy* h, const nmg_solve_opts* opts, int nrh
     NMG_TRY(finish_op(h));
     int f[FLAG_COUNT];
     NMG_CK(cudaMemcpy(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost));
-    if (f[FLAG_ABORT]) {
-        cudaMemset(h->flags + FLAG_ABORT, 0, sizeof(int));
+    if (f[FLAG_MANY]) {
+        cudaMemset(h->flags + FLAG_MANY, 0, sizeof(int));
         return fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
     }
     return NMG_OK;
@@ -2029,6 +2029,19 @@ static void advance_group(Server* S, Group* G, cudaError_t q, std::vector<Reques
         job_advance(r->job);
         r->job.launches += g_launches - l0;
         if (r->job.phase == SolveJob::P_WANT) want[nw++] = k;
+    }
+    // before a column leaves: a bounded wait of the shared multi-vector apply
+    // that ran out fails every column of the group
+    bool leaving = false;
+    for (int k = 0; k < kMaxCols; ++k) leaving = leaving || (G->col[k] && G->col[k]->job.phase == SolveJob::P_DONE);
+    int many_flag = 0;   // read in the hierarchy's stream order (no device-wide synchronisation)
+    if (leaving &&
+        cudaMemcpyAsync(&many_flag, h->flags + FLAG_MANY, sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+        cudaStreamSynchronize(h->stream) == cudaSuccess && many_flag) {
+        cudaMemsetAsync(h->flags + FLAG_MANY, 0, sizeof(int), h->stream);
+        fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
+        for (int k = 0; k < kMaxCols; ++k)
+            if (G->col[k]) job_fail(G->col[k]->job, NMG_ERR_TIMEOUT);
     }
     for (int k = 0; k < kMaxCols; ++k)
         if (G->col[k] && G->col[k]->job.phase == SolveJob::P_DONE) finish_grouped(S, G->col[k], active, res);

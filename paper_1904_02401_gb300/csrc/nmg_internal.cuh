@@ -147,7 +147,11 @@ struct Hierarchy {
 };
 
 // Error flags (device int array)
-enum Flag { FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_ABORT = 3, FLAG_COUNT = 4 };
+// FLAG_ABORT: the persistent V-cycle gave up a bounded wait; FLAG_MANY: the
+// multi-vector apply did.
+enum Flag {
+    FLAG_BAD_PATTERN = 0, FLAG_NONFINITE = 1, FLAG_SINGULAR = 2, FLAG_ABORT = 3, FLAG_MANY = 4, FLAG_COUNT = 5
+};
 
 // Persistent V-cycle (persistent.cu) on the finest level's buffers of precision prec.
 struct Hierarchy;
