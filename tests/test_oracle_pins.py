@@ -356,6 +356,30 @@ def test_two_level_coarse_correction_bruteforce(dim):
     np.testing.assert_allclose(h.vcycle(r), ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_vcycle_is_linear_and_stateless(dim):
+    """A V-cycle that starts every level from zero (Sec. 4.3 (II)) applies one
+    fixed linear operator to its input: V(a r1 + b r2) = a V(r1) + b V(r2) to
+    rounding, and a repeated call returns the same vector bit for bit (no state
+    carried between applications).  A lost zero start or an iterate kept from
+    the previous call breaks either; many right-hand sides can therefore be
+    preconditioned column by column."""
+    sysm = build_system(small_problem(dim, 8 if dim == 2 else 4, 2))
+    h = Hierarchy(sysm.levels, sysm.dirichlet)
+    rng = np.random.default_rng(9)
+    mask = sysm.dirichlet.astype(bool)
+    r1, r2 = rng.standard_normal(sysm.rhs.size), rng.standard_normal(sysm.rhs.size)
+    r1[mask] = 0.0
+    r2[mask] = 0.0
+    a, b = 1.7, -0.3
+    z1 = h.vcycle(r1)
+    z2 = h.vcycle(r2)
+    lhs = h.vcycle(a * r1 + b * r2)
+    assert np.linalg.norm(lhs - (a * z1 + b * z2)) <= 1e-12 * np.linalg.norm(a * z1 + b * z2)
+    assert np.array_equal(h.vcycle(r1), z1)
+    assert np.linalg.norm(z1) > 0
+
+
 # ----------------------------------------------------------------------------
 # whole solve against dense direct solves (P2)
 # ----------------------------------------------------------------------------
