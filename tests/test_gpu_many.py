@@ -203,3 +203,25 @@ def test_many_refusals_and_bytes(nmg, built, sessions):
     B9 = torch.from_numpy(_columns(s, 8, 16)).cuda()
     S.solve_many(B9, torch.zeros_like(B9), 8, precision=1)
     assert S.bytes() >= before
+
+
+@pytest.mark.parametrize("case", ["2d_24x40_3lev", "3d_8x12x16_3lev"])
+@pytest.mark.parametrize("nu", [(0, 2), (1, 1), (2, 0), (3, 1)])
+@pytest.mark.parametrize("weighting", [0, 1])
+def test_vcycle_many_smoothing_variants(nmg, built, sessions, case, nu, weighting):
+    """Other pre/post-smoothing counts (including none before or after), both
+    overlap weightings and another damping: still equal to the single V-cycle
+    per column bit for bit, plain launches and graph replay alike."""
+    from paper_1904_02401_gb300.session import solve_opts
+    s, _, _ = built[case]
+    S = sessions[case]
+    R = torch.from_numpy(_columns(s, 5, 17).astype(np.float32)).cuda()
+    kw = dict(precision=1, nu1=nu[0], nu2=nu[1], weighting=weighting, omega=0.7)
+    for graph in (0, 1):
+        Z = torch.full_like(R, float("nan"))
+        nmg.check(nmg.nmg_vcycle_many(S.handle, solve_opts(use_graph=graph, **kw), 5, R, Z))
+        for k in (0, 4):
+            z = torch.zeros_like(R[k])
+            nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(use_graph=0, engine=nmg.NMG_ENGINE_KERNELS, **kw),
+                                     R[k].contiguous(), z))
+            assert torch.equal(Z[k], z), (graph, k)
