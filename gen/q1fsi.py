@@ -427,13 +427,16 @@ def ale_fixed_nodes(dim: int, cells: tuple, solid_mask: np.ndarray) -> np.ndarra
     return fixed
 
 
-def assemble_ale_level(problem: Problem, cells: tuple, coarse_cells: Optional[tuple] = None) -> LevelMatrix:
+def assemble_ale_level(problem: Problem, cells: tuple, coarse_cells: Optional[tuple] = None,
+                       eliminate: bool = True) -> LevelMatrix:
     """The ALE-extension operator on one level: the harmonic extension of the
     solid deformation into the fluid, one Q1 Laplacian per displacement
     component, (grad u_c, grad phi_c) summed over the fluid cells (2^d-point
     Gauss quadrature).  Rows and columns of the fixed nodes (ale_fixed_nodes)
     are those of the identity; their given values enter through the
-    right-hand side."""
+    right-hand side.  eliminate=False returns the operator before that step
+    (every row and column as assembled), whose free rows carry the coupling
+    E_{f,i} of the extension equation to the given values."""
     dim = problem.dim
     nc = dim
     na = 2 ** dim
@@ -454,6 +457,8 @@ def assemble_ale_level(problem: Problem, cells: tuple, coarse_cells: Optional[tu
             pb = tuple((b >> m) & 1 for m in range(dim))
             s = sum((pb[m] - pa[m] + 1) * 3 ** m for m in range(dim))
             S[rows + (s,)] += (fluid * G[a, b])[..., None, None] * eye
+    if not eliminate:
+        return _stencil_to_bsr(S, dim, cells, nc)
     fixed = ale_fixed_nodes(dim, cells, solid)
     S[fixed] = 0.0
     offs = _offsets(dim)

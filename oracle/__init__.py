@@ -14,6 +14,7 @@ method of Section 4.3 in float64:
 * ``multigrid`` the V-cycle preconditioner of item (II)
 * ``fgmres``    the outer flexible GMRES of item (I)
 * ``solver``    the whole solve
+* ``coupling``  problems (2) and (3) of Section 4.2 around the momentum solve
 
 Where the paper is silent (transfers, coarse solver, stopping norm, GMRES
 variant) each module states the reading it implements.
