@@ -380,6 +380,116 @@ def test_vcycle_is_linear_and_stateless(dim):
     assert np.linalg.norm(z1) > 0
 
 
+def _dense_patch_smoother(Ad, cells, nc, omega, weighting):
+    """S = omega W sum_i R_i^T (R_i A R_i^T)^{-1} R_i as a dense matrix, the patch
+    dof sets found from node coordinates (the 3^d nodes of each 2^d-cell block)."""
+    coords = node_coords(cells)
+    n = Ad.shape[0]
+    S = np.zeros((n, n))
+    count = np.zeros(n)
+    for origin in itertools.product(*[range(0, c, 2) for c in cells]):
+        inside = np.all((coords >= np.array(origin)) & (coords <= np.array(origin) + 2), axis=1)
+        dof = (np.nonzero(inside)[0][:, None] * nc + np.arange(nc)).reshape(-1)
+        S[np.ix_(dof, dof)] += np.linalg.inv(Ad[np.ix_(dof, dof)])
+        count[dof] += 1
+    w = 1.0 / count if weighting == "average" else np.ones(n)
+    return omega * w[:, None] * S
+
+
+def _dense_interpolation(fcells, ccells, nc):
+    """Q1 nodal interpolation by coordinates: fine node x gets weight
+    prod_m (1 if x_m = 2 X_m, 1/2 if |x_m - 2 X_m| = 1) from coarse node X."""
+    Xf, Xc = node_coords(fcells), node_coords(ccells)
+    dist = np.abs(Xf[:, None, :] - 2 * Xc[None, :, :])
+    w = np.prod(np.where(dist == 0, 1.0, np.where(dist == 1, 0.5, 0.0)), axis=2)
+    return np.kron(w, np.eye(nc))
+
+
+def _dense_vcycle_matrix(sysm, nu1, nu2, omega, weighting):
+    """The V(nu1, nu2) preconditioner as one dense matrix, through the error
+    propagation identity of a consistent linear iteration started from zero:
+    z = M b with M = (I - E) A^{-1}, E = (I - S A)^nu2 (I - C A) (I - S A)^nu1,
+    C = Z_f P M_c Z_c P^T (the coarse-grid correction with the Dirichlet
+    entries of the restricted residual and of the prolonged correction
+    zeroed), M_0 = A_0^{-1}.  Nothing here steps through the cycle."""
+    nc = sysm.problem.ncomp
+    lv = sysm.levels
+    mats = [BlockMatrix(l.row_ptr, l.col_idx, l.vals).dense() for l in lv]
+    # Dirichlet unknowns of every level: coarse node X is fine node 2X
+    masks = [None] * len(lv)
+    masks[-1] = sysm.dirichlet.astype(bool)
+    for lev in range(len(lv) - 1, 0, -1):
+        Xf, Xc = node_coords(lv[lev].cells), node_coords(lv[lev - 1].cells)
+        fine_of = [int(np.argmin(np.abs(Xf - 2 * xc).sum(1))) for xc in Xc]
+        masks[lev - 1] = masks[lev].reshape(-1, nc)[fine_of].reshape(-1)
+    M = np.linalg.inv(mats[0])
+    for lev in range(1, len(lv)):
+        A = mats[lev]
+        n = A.shape[0]
+        I = np.eye(n)
+        S = _dense_patch_smoother(A, lv[lev].cells, nc, omega, weighting)
+        P = _dense_interpolation(lv[lev].cells, lv[lev - 1].cells, nc)
+        Zf = np.diag((~masks[lev]).astype(float))
+        Zc = np.diag((~masks[lev - 1]).astype(float))
+        C = Zf @ P @ M @ Zc @ P.T
+        Es = I - S @ A
+        E = np.linalg.matrix_power(Es, nu2) @ (I - C @ A) @ np.linalg.matrix_power(Es, nu1)
+        M = (I - E) @ np.linalg.inv(A)
+    return M
+
+
+@pytest.mark.parametrize("dim,n,levels", [(2, 8, 2), (2, 16, 3), (3, 4, 2), (3, 8, 3)])
+@pytest.mark.parametrize("nu,omega,weighting", [((1, 1), 0.8, "average"), ((2, 2), 0.8, "average"),
+                                                ((2, 1), 0.8, "average"), ((1, 2), 0.3, "sum")])
+def test_vcycle_composition_against_error_propagation(dim, n, levels, nu, omega, weighting):
+    """The oracle's V(nu1, nu2) cycle (Sec. 4.3 (II) with the smoother of
+    Eq. (vanka)) on 2 and 3 levels equals the dense operator (I - E) A^{-1}
+    built from the error propagation matrix of its stages.  The dense side
+    finds patch dofs, interpolation weights and coarse Dirichlet entries from
+    node coordinates.  Restricting b instead of b - A x, post-smoothing the
+    uncorrected iterate, swapping nu1 and nu2, or dropping a Dirichlet zeroing
+    each change M."""
+    sysm = build_system(small_problem(dim, n, levels, solid=(dim - 1, -1, 0.5)))
+    h = Hierarchy(sysm.levels, sysm.dirichlet, nu1=nu[0], nu2=nu[1], omega=omega, weighting=weighting)
+    M = _dense_vcycle_matrix(sysm, nu[0], nu[1], omega, weighting)
+    rng = np.random.default_rng(21)
+    for _ in range(2):
+        r = rng.standard_normal(sysm.rhs.size)
+        ref = M @ r
+        got = h.vcycle(r)
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("slip", ["restrict_b", "post_from_uncorrected", "swap_nu"])
+def test_vcycle_composition_pin_detects_slips(slip, monkeypatch):
+    """Each plausible slip, planted in the oracle's V-cycle on the CPU, moves
+    it away from the error-propagation operator by far more than the pin's
+    tolerance (the pin above is not vacuous).  Dropping the Dirichlet zeroing
+    of the prolonged correction is not among them: with velocity Dirichlet
+    data on the whole boundary the coarse correction already vanishes on the
+    boundary nodes (identity rows, zeroed residual entries, and fine boundary
+    nodes interpolated from coarse boundary nodes only), so that zeroing does
+    not change the result on these meshes."""
+    sysm = build_system(small_problem(2, 8, 2, solid=(1, -1, 0.5)))
+    M = _dense_vcycle_matrix(sysm, 2, 1, 0.8, "average")
+    h = Hierarchy(sysm.levels, sysm.dirichlet, nu1=2, nu2=1)
+    if slip == "restrict_b":
+        def restrict_residual(lev, b, x):
+            rc = h.levels[lev].P.T @ b
+            rc[h.levels[lev - 1].mask] = 0.0
+            return rc
+        monkeypatch.setattr(h, "restrict_residual", restrict_residual)
+    elif slip == "post_from_uncorrected":
+        orig = h.prolongate
+        monkeypatch.setattr(h, "prolongate", lambda lev, ec: 0.0 * orig(lev, ec))
+    else:
+        h.nu1, h.nu2 = 1, 2
+    r = np.random.default_rng(21).standard_normal(sysm.rhs.size)
+    ref = M @ r
+    assert np.linalg.norm(h.vcycle(r) - ref) > 1e-8 * np.linalg.norm(ref)
+
+
 # ----------------------------------------------------------------------------
 # whole solve against dense direct solves (P2)
 # ----------------------------------------------------------------------------
