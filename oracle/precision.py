@@ -70,3 +70,47 @@ def with_stored_inverses(hierarchy, fmt: str):
             c.Ainv = round_storage(L.Ainv, fmt)
         h.levels.append(c)
     return h
+
+
+class _Float32Matrix:
+    """A level matrix rounded to binary32 whose products run in binary32."""
+
+    def __init__(self, A):
+        self.csr = A.csr.astype(np.float32)
+        self.ncomp = A.ncomp
+        self.nodes = A.nodes
+
+    @property
+    def size(self) -> int:
+        return self.nodes * self.ncomp
+
+    def matvec(self, x):
+        return self.csr @ x
+
+
+def with_fp32_arithmetic(hierarchy, fmt: str):
+    """A copy of an oracle Hierarchy that runs the V-cycle the way the
+    reduced-precision path does: level matrices, transfers, overlap weights and
+    every vector in binary32 (NumPy float32 arithmetic), patch inverses rounded
+    to the storage format fmt ("fp32" or "bf16") and held as binary32, and the
+    coarsest level solved exactly in FP64 with the result rounded to binary32.
+    Call its vcycle with a float32 vector.  The tests use how far this copy's
+    result lies from the FP64 oracle's as the scale of the rounding errors of
+    the reduced-precision V-cycle (summation orders differ from any GPU
+    kernel's, so it is a model of their size, not of their values)."""
+    import scipy.linalg as sla
+    h = copy.copy(hierarchy)
+    h.levels = []
+    for L in hierarchy.levels:
+        c = copy.copy(L)
+        c.A = _Float32Matrix(L.A)
+        if L.Ainv is not None:
+            c.Ainv = round_storage(L.Ainv, fmt).astype(np.float32)
+            c.weight = L.weight.astype(np.float32)
+        if L.P is not None:
+            c.P = L.P.astype(np.float32)
+        h.levels.append(c)
+    h.omega = np.float32(hierarchy.omega)
+    lu = hierarchy.coarse_lu
+    h.coarse_solve = lambda b: sla.lu_solve(lu, np.asarray(b, dtype=np.float64)).astype(np.float32)
+    return h

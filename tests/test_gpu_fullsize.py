@@ -11,6 +11,8 @@ caller-owned stream).
   the solves by properties that hold at any size (true FP64 residual <= 1e-8).
 """
 
+import os
+
 import numpy as np
 import pytest
 
@@ -215,3 +217,113 @@ def test_96cube_multi_vector(big, prec):
             assert infos[k].iterations == info.iterations
             assert torch.equal(X[k], x)
             assert _true_rel_residual(s.fine, cols[k], X[k].cpu().numpy()) <= 1e-8
+
+
+# ----------------------------------------------------------------------------
+# FP32 / BF16 paths at 96^3 node by node: every CTA of the streaming Vanka
+# apply walks many more chunks than its ring has stages (tests/rounding_bounds.py
+# states the tolerances)
+# ----------------------------------------------------------------------------
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "vcycle_96cube_oracle.txt")
+
+
+def _golden_vcycle():
+    """The FP64 oracle's V(2,2) cycle of the workload's right-hand side at
+    sampled nodes (tests/golden/make_vcycle_96cube.py), with its largest entry
+    and, per component, how far the binary32 model of the cycle lies from it."""
+    head = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("# max_abs"):
+                key, *vals = line[2:].split()
+                head[key] = np.array([float(v) for v in vals])
+    data = np.loadtxt(GOLDEN)
+    return data[:, 0].astype(np.int64), data[:, 1:], head
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_96cube_one_vanka_step_sampled(big, prec):
+    """One FP32/BF16 Vanka step from a random iterate at sampled nodes, each
+    entry within its first-order rounding bound."""
+    from oracle.bsr import BlockMatrix
+    from oracle.mesh import patch_nodes
+    from paper_1904_02401_gb300 import nmg
+    from rounding_bounds import to_storage32, vanka_step_and_bound
+    s, S, stream = big
+    L = len(s.levels) - 1
+    fine = s.fine
+    nc, dim = 4, 3
+    A = BlockMatrix(fine.row_ptr, fine.col_idx, fine.vals)
+    pn = patch_nodes(fine.cells)
+    rng = np.random.default_rng(12 + prec)
+    b = to_storage32(rng.uniform(-1, 1, s.unknowns))
+    x0 = to_storage32(rng.uniform(-1, 1, s.unknowns))
+    targets = _sample_nodes(fine, rng, 80)
+    plist = {int(t): np.nonzero((pn == t).any(axis=1))[0] for t in targets}
+    patches = np.unique(np.concatenate(list(plist.values())))
+    pnodes = np.unique(pn[patches])
+    d = np.zeros(s.unknowns)
+    abs_ax = np.zeros(s.unknowns)
+    absA = type(fine)(fine.cells, fine.row_ptr, fine.col_idx, np.abs(fine.vals))
+    rows = (pnodes[:, None] * nc + np.arange(nc)).reshape(-1)
+    d[rows] = b[rows] - _row_products(fine, x0, pnodes).reshape(-1)
+    abs_ax[rows] = _row_products(absA, np.abs(x0), pnodes).reshape(-1)
+    nodes = pn[patches]
+    Ap = A.block_lookup(nodes[:, :, None], nodes[:, None, :]).transpose(0, 1, 3, 2, 4).reshape(
+        patches.size, 27 * nc, 27 * nc)
+    inv = np.linalg.inv(Ap)
+    dofs = (nodes[:, :, None] * nc + np.arange(nc)).reshape(patches.size, -1)
+    w = np.ones(s.unknowns)
+    for t, pl in plist.items():
+        w[t * nc:(t + 1) * nc] = 1.0 / len(pl)
+    ref, bound = vanka_step_and_bound(inv, dofs, b, x0, d, abs_ax, w, 0.8, prec, dim, nc)
+    xd = torch.from_numpy(x0.astype(np.float32)).cuda()
+    with torch.cuda.stream(stream):
+        nmg.check(nmg.nmg_smooth(S.handle, L, prec, torch.from_numpy(b.astype(np.float32)).cuda(), xd, 1, 0, 0.8,
+                                 nmg.NMG_WEIGHT_AVERAGE))
+    stream.synchronize()
+    got = xd.double().cpu().numpy()
+    sel = (np.array(sorted(plist))[:, None] * nc + np.arange(nc)).reshape(-1)
+    err = np.abs(got[sel] - ref[sel])
+    assert np.all(err <= bound[sel]), (err / bound[sel]).max()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("many", [False, True])
+def test_96cube_vcycle_sampled_against_oracle(big, prec, many):
+    """The FP32/BF16 V(2,2) cycle of the workload's right-hand side (graph
+    replay, as the solve runs it), and column 0 and 5 of an 8-column
+    multi-vector cycle, against the FP64 oracle's cycle at 1,114 sampled
+    nodes."""
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    from rounding_bounds import vcycle_tolerance, within
+    s, S, stream = big
+    nodes, zref, head = _golden_vcycle()
+    nc = 4
+    tol = vcycle_tolerance(head["max_abs_dz_%s_model" % {1: "fp32", 2: "bf16"}[prec]], head["max_abs_z"][0], nc)
+    r = torch.from_numpy(s.rhs.astype(np.float32)).cuda()
+    outs = []
+    with torch.cuda.stream(stream):
+        if many:
+            rng = np.random.default_rng(8)
+            mask = s.dirichlet.astype(bool)
+            cols = []
+            for k in range(8):
+                v = s.rhs.astype(np.float32) if k in (0, 5) else rng.uniform(-1, 1, s.unknowns).astype(np.float32)
+                v[mask] = 0.0
+                cols.append(v)
+            R = torch.from_numpy(np.stack(cols)).cuda()
+            Z = torch.full_like(R, float("nan"))
+            nmg.check(nmg.nmg_vcycle_many(S.handle, solve_opts(precision=prec, use_graph=1), 8, R, Z))
+            outs = [Z[0], Z[5]]
+        else:
+            z = torch.zeros_like(r)
+            nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=1), r, z))
+            outs = [z]
+    stream.synchronize()
+    for z in outs:
+        got = z.double().cpu().numpy().reshape(-1, nc)[nodes]
+        err = got - zref
+        assert within(err, tol, nc).all(), (np.abs(err).max(axis=0), tol)

@@ -60,3 +60,25 @@ def test_stored_inverses_copy_leaves_the_hierarchy_alone():
     assert hb.fine.A is h.fine.A
     z, zb = h.vcycle(s.rhs), hb.vcycle(s.rhs)
     assert 0 < np.abs(zb - z).max() <= 1e-2 * np.abs(z).max()
+
+
+def test_fp32_model_runs_in_binary32_and_stays_near_the_oracle():
+    """The binary32 model of the V-cycle computes in float32 and lies within a
+    few thousand binary32 roundings of the FP64 cycle (FP32 inverses), and
+    within the bfloat16 rounding scale with BF16 inverses; the FP64 hierarchy
+    it was copied from is untouched."""
+    from gen import Problem, build_system
+    from oracle.multigrid import Hierarchy
+    from oracle.precision import with_fp32_arithmetic
+    s = build_system(Problem(dim=2, n=(16, 16), levels=3, solid=(0, +1, 0.6)))
+    h = Hierarchy(s.levels, s.dirichlet)
+    r = s.rhs.astype(np.float32)
+    z = h.vcycle(r.astype(np.float64))
+    inv = h.fine.Ainv.copy()
+    z32 = with_fp32_arithmetic(h, "fp32").vcycle(r)
+    zbf = with_fp32_arithmetic(h, "bf16").vcycle(r)
+    assert z32.dtype == np.float32 and zbf.dtype == np.float32
+    assert np.array_equal(h.fine.Ainv, inv) and h.vcycle(r.astype(np.float64)).dtype == np.float64
+    m = np.abs(z).max()
+    assert 0 < np.abs(z32 - z).max() <= 1e3 * 2.0 ** -24 * m
+    assert np.abs(z32 - z).max() < np.abs(zbf - z).max() <= 2.0 ** -8 * m
