@@ -226,6 +226,13 @@ nmg_status nmg_server_set_batching(nmg_server* s, int max_columns);
 nmg_status nmg_submit(nmg_server* s, nmg_hierarchy* h, const double* b, double* x,
                       const nmg_solve_opts* opts, uint64_t* ticket);
 nmg_status nmg_poll(nmg_server* s, uint64_t ticket, int timeout_ms, nmg_solve_info* info);
+/* Device memory held for the server's running requests, in bytes: the
+ * hierarchies with a running request (each once), the server's workspace
+ * clones and the column workspaces of groups with running columns.  This is
+ * the quantity the memory budget bounds.  *resident_bytes: the value after the
+ * worker's last round; *peak_bytes: the largest value since the server was
+ * created.  Either pointer may be NULL.  NMG_ERR_INVALID for a NULL server. */
+nmg_status nmg_server_memory(nmg_server* s, size_t* resident_bytes, size_t* peak_bytes);
 /* Finishes every queued and running request, then stops the server. */
 nmg_status nmg_server_destroy(nmg_server* s);
 
@@ -303,6 +310,17 @@ nmg_status nmg_profile_enable(nmg_hierarchy* h, int mode);
  * vector it must read or write once). */
 nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launches,
                             double* bytes_per_launch);
+
+/* Iteration limit of the grid-barrier wait of the persistent V-cycle engine
+ * (NMG_ENGINE_PERSISTENT) on this hierarchy; 0 restores the default (2^24
+ * polls, far beyond any barrier of a running V-cycle).  Every device-side wait
+ * of the library is bounded: a wait that runs out sets a device flag, the
+ * waiting CTAs leave the kernel, and the solve or V-cycle returns
+ * NMG_ERR_TIMEOUT with the flag cleared, so the next call runs normally.  A
+ * small limit makes that path testable without a fault (a limit of 1 lets
+ * every barrier wait run out).  No counterpart in the paper.  NMG_ERR_INVALID
+ * for a NULL hierarchy or a negative limit. */
+nmg_status nmg_set_wait_limit(nmg_hierarchy* h, int spins);
 
 /* ---- one Vanka correction that allocates no device memory.  The paper has no
  * counterpart: this call exists for callers that cannot let a library call

@@ -837,6 +837,27 @@ static nmg_status ensure_krylov(Hierarchy* h, int m) {
     return NMG_OK;
 }
 
+// Bytes ensure_krylov(h, m) would add to h->bytes (0 when the bases already hold m).
+static size_t krylov_growth(const Hierarchy* h, int m) {
+    if (h->m_alloc >= m) return 0;
+    const Geom& g = h->lev[h->L - 1].g;
+    const size_t vec = (size_t)g.nodes * g.nc * sizeof(double);
+    const size_t held = h->V ? (size_t)(2 * h->m_alloc + 1) * vec : 0;
+    return (size_t)(2 * m + 1) * vec - held;
+}
+
+// Bytes ensure_many(h, K) would add to h->bytes (0 when the buffers already hold K columns).
+static size_t many_growth(const Hierarchy* h, int K) {
+    if (h->many_k >= K) return 0;
+    size_t add = 0, held = 0;
+    for (int l = 0; l < h->L; ++l)
+        for (int w = 0; w < 4; ++w) {
+            add += std::max<size_t>(16, many_level_bytes(h->lev[l].g, l, K, w));
+            if (h->many_k) held += std::max<size_t>(16, many_level_bytes(h->lev[l].g, l, h->many_k, w));
+        }
+    return add - held;
+}
+
 static bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1145,16 +1166,19 @@ static void job_advance(SolveJob& J) {
     }
     case SolveJob::P_FINISH: {
         const int* f = h->host_flags;
+        // a wait that ran out left the preconditioner's result incomplete: that is the cause of
+        // whatever the iteration reported afterwards (no convergence, a non-finite norm)
+        const bool overridable = J.st == NMG_OK || J.st == NMG_ERR_NOT_CONVERGED || J.st == NMG_ERR_NONFINITE;
         if (f[FLAG_COUNT]) {
             wait_timeout_clear(h->stream);
-            if (J.st == NMG_OK) {
+            if (overridable) {
                 fail(NMG_ERR_TIMEOUT, "a bounded device wait ran out (TMA copy)");
                 job_fail(J, NMG_ERR_TIMEOUT);
             }
         }
         if (f[FLAG_ABORT]) {
             cudaMemsetAsync(h->flags + FLAG_ABORT, 0, sizeof(int), h->stream);
-            if (J.st == NMG_OK) {
+            if (overridable || J.st == NMG_ERR_TIMEOUT) {
                 fail(NMG_ERR_TIMEOUT, "the persistent V-cycle aborted (grid barrier or copy wait ran out)");
                 job_fail(J, NMG_ERR_TIMEOUT);
             }
@@ -1857,6 +1881,12 @@ nmg_status nmg_autotune_report(nmg_hierarchy* h, char* buf, size_t len) {
     return NMG_OK;
 }
 
+nmg_status nmg_set_wait_limit(nmg_hierarchy* h, int spins) {
+    if (!h || spins < 0) return fail(NMG_ERR_INVALID, "NULL hierarchy or negative limit");
+    h->wait_limit = spins;
+    return NMG_OK;
+}
+
 nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launches, double* bytes_per_launch) {
     if (!h) return fail(NMG_ERR_INVALID, "NULL hierarchy");
     NMG_CK(cudaStreamSynchronize(h->stream));
@@ -1891,6 +1921,7 @@ nmg_status nmg_profile_read(nmg_hierarchy* h, double* ms_total, int64_t* launche
 // kernels in the same order as nmg_solve, so a result does not depend on what
 // else runs beside it.
 // ---------------------------------------------------------------------------
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -1930,7 +1961,6 @@ struct Group {
     Request* col[kMaxCols] = {};
     int n = 0;                    // occupied columns
     nmg_solve_opts vo{};          // the V-cycle options its columns share
-    size_t ws_bytes = 0;          // bytes of the column workspaces, taken while columns run
     cudaEvent_t ev = nullptr;
     bool inflight = false;        // work enqueued since the last round
 };
@@ -1949,7 +1979,8 @@ struct Server {
     // workspace clones per hierarchy (server thread only), kept until the server stops;
     // at most extra_workspaces per hierarchy (0: one request per hierarchy at a time)
     std::unordered_map<Hierarchy*, std::vector<Hierarchy*>> clones;
-    size_t clone_bytes = 0;
+    // bytes of the running requests' hierarchies and workspaces: now, and the most since creation
+    std::atomic<size_t> resident{0}, peak{0};
     int extra_workspaces = 0;
     int batch_columns = 0;        // > 1: FP32 / BF16 requests on one hierarchy run as a column group
     std::unordered_map<Hierarchy*, Group*> groups;
@@ -1962,22 +1993,36 @@ static bool same_vcycle(const nmg_solve_opts& a, const nmg_solve_opts& b) {
 
 static Hierarchy* column_workspace(Hierarchy* h, int k) { return k == 0 ? h : h->many_ws[k - 1]; }
 
-// Memory the running requests hold: each hierarchy with a running request
-// once (its operator and first workspace), plus every workspace clone.
+// Hierarchies with running requests.  The memory they hold is read from their
+// live byte counts (each such hierarchy once: its operator and first
+// workspace), so buffers a request allocates while it runs (Krylov bases,
+// multi-vector level buffers) are counted as soon as they exist, and nothing
+// is subtracted that was not added.
 struct Residency {
     std::unordered_map<Hierarchy*, int> running;   // requests per submitted hierarchy
-    size_t bytes = 0;
-    void add(Hierarchy* h) {
-        if (running[h]++ == 0) bytes += h->bytes;
-    }
+    void add(Hierarchy* h) { running[h]++; }
     void remove(Hierarchy* h) {
-        if (--running[h] == 0) {
-            bytes -= h->bytes;
-            running.erase(h);
-        }
+        if (--running[h] == 0) running.erase(h);
     }
-    size_t with(Hierarchy* h) const { return running.count(h) ? 0 : h->bytes; }   // bytes h would add
+    bool has(Hierarchy* h) const { return running.count(h) != 0; }
+    size_t bytes() const {
+        size_t s = 0;
+        for (const auto& kv : running) s += kv.first->bytes;
+        return s;
+    }
 };
+
+// Live bytes of the server's workspace clones and of the column workspaces of
+// groups with running columns (a group without columns may outlive its hierarchy).
+static size_t workspace_bytes(const Server* S) {
+    size_t s = 0;
+    for (const auto& kv : S->clones)
+        for (const Hierarchy* c : kv.second) s += c->bytes;
+    for (const auto& kv : S->groups)
+        if (kv.second->n > 0)
+            for (const Hierarchy* c : kv.first->many_ws) s += c->bytes;
+    return s;
+}
 
 static void finish_request(Server* S, Request* r, std::vector<Request*>& active, std::unordered_set<Hierarchy*>& busy,
                            Residency& res) {
@@ -2091,40 +2136,49 @@ static void server_loop(Server* S) {
                 continue;
             }
             // in arrival order: a request starts on its hierarchy, or on an idle clone of it, or on a
-            // new clone if the budget holds one more workspace; otherwise it waits
-            S->clone_bytes = 0;
-            for (auto& kv : S->clones)
-                for (Hierarchy* c : kv.second) S->clone_bytes += c->bytes;
-            for (auto& kv : S->groups)   // (a group without columns may outlive its hierarchy)
-                if (kv.second->n > 0) S->clone_bytes += kv.second->ws_bytes;
+            // new clone if the budget holds one more workspace; otherwise it waits.  The budget is
+            // checked against the live bytes of the running hierarchies and workspaces plus what the
+            // request will add: its hierarchy (once), the Krylov bases its slot still has to
+            // allocate, and for a column group the multi-vector buffers and column workspaces.
+            size_t pending = 0;   // growth of the requests admitted in this pass (allocated when they start)
             for (auto it = S->queue.begin(); it != S->queue.end() && (int)(active.size() + admit.size()) < S->max_slots;) {
                 Request* r = *it;
-                const size_t used = res.bytes + S->clone_bytes;
-                const size_t need = res.with(r->h);
-                bool fits = S->budget == 0 || used + need <= S->budget || (active.empty() && admit.empty());
+                const size_t used = res.bytes() + workspace_bytes(S) + pending;
+                const size_t base = res.has(r->h) ? 0 : r->h->bytes;
+                const bool first = active.empty() && admit.empty();   // always admitted (alone it fits or fails)
+                auto fits_with = [&](size_t need) { return S->budget == 0 || used + need <= S->budget || first; };
                 Hierarchy* slot = nullptr;
                 Group* G = S->groups.count(r->h) ? S->groups[r->h] : nullptr;
                 const bool batch = S->batch_columns > 1 && r->o.precision != NMG_PREC_FP64;
-                if (fits && batch) {
+                if (batch) {
                     // a column of the hierarchy's group (none runs alone on it)
-                    if (!busy.count(r->h) && (!G || G->n == 0 || (G->n < S->batch_columns && same_vcycle(G->vo, r->o)))) {
-                        int k = -1;
+                    int k = -1;
+                    if (fits_with(base) && !busy.count(r->h) &&
+                        (!G || G->n == 0 || (G->n < S->batch_columns && same_vcycle(G->vo, r->o))))
                         for (int c = 0; c < S->batch_columns && k < 0; ++c)
                             if (!G || !G->col[c]) k = c;
-                        if (k >= 0 && many_workspaces(r->h, k + 1) == NMG_OK) {
+                    size_t ws_before = 0;
+                    for (Hierarchy* c : r->h->many_ws) ws_before += c->bytes;
+                    if (k >= 0 && many_workspaces(r->h, k + 1) == NMG_OK) {
+                        size_t ws_now = 0;
+                        for (Hierarchy* c : r->h->many_ws) ws_now += c->bytes;
+                        const bool counted = G && G->n > 0;   // the group's workspaces are already in used
+                        const size_t grow = many_growth(r->h, S->batch_columns > 4 ? 8 : 4) +
+                                            krylov_growth(column_workspace(r->h, k), r->o.restart);
+                        const size_t need = base + grow + (counted ? ws_now - ws_before : ws_now);
+                        if (fits_with(need)) {
                             if (!G) {
                                 G = new Group();
                                 G->h = r->h;
                                 S->groups[r->h] = G;
                             }
                             if (G->n == 0) G->vo = r->o;
-                            G->ws_bytes = 0;
-                            for (Hierarchy* c : r->h->many_ws) G->ws_bytes += c->bytes;
                             G->col[k] = r;
                             G->n++;
                             r->group = G;
                             r->col = k;
                             res.add(r->h);
+                            pending += grow;
                             r->slot = column_workspace(r->h, k);
                             admit.push_back(r);
                             it = S->queue.erase(it);
@@ -2134,13 +2188,19 @@ static void server_loop(Server* S) {
                     ++it;
                     continue;
                 }
-                if (fits && G && G->n > 0) fits = false;   // the hierarchy runs a column group
-                if (fits) {
+                if (!(G && G->n > 0)) {   // (a hierarchy running a column group takes no lone request)
                     if (!busy.count(r->h)) slot = r->h;
                     for (size_t c = 0; !slot && c < S->clones[r->h].size(); ++c)
                         if (!busy.count(S->clones[r->h][c])) slot = S->clones[r->h][c];
-                    if (!slot && (int)S->clones[r->h].size() < S->extra_workspaces) {
-                        const size_t room = S->budget == 0 ? 0 : (S->budget > used + need ? S->budget - used - need : 1);
+                    if (slot) {
+                        const size_t grow = krylov_growth(slot, r->o.restart);
+                        if (fits_with(base + grow)) {
+                            pending += grow;
+                        } else {
+                            slot = nullptr;
+                        }
+                    } else if ((int)S->clones[r->h].size() < S->extra_workspaces && fits_with(base)) {
+                        const size_t room = S->budget == 0 ? 0 : (S->budget > used + base ? S->budget - used - base : 1);
                         Hierarchy* c = nullptr;
                         if (clone_workspace(r->h, room, &c) == NMG_OK) {
                             if (ensure_krylov(c, r->o.restart) == NMG_OK) {   // the Krylov bases inside the budget too
@@ -2186,6 +2246,16 @@ static void server_loop(Server* S) {
                 }
                 r->job.grouped = true;
                 r->job.launches = g_launches - l0;
+                // the multi-vector level buffers the group's V-cycles use, sized for the group's
+                // largest column count now (admission counted them)
+                if (r->job.phase != SolveJob::P_DONE) {
+                    const nmg_status sm = ensure_many(h, S->batch_columns > 4 ? 8 : 4);
+                    if (sm != NMG_OK) {
+                        r->job.st = sm;
+                        r->job.err = g_last_error;
+                        r->job.phase = SolveJob::P_DONE;
+                    }
+                }
                 Group* G = r->group;
                 if (!G->ev && cudaEventCreateWithFlags(&G->ev, cudaEventDisableTiming) != cudaSuccess) G->ev = nullptr;
                 if (G->ev) {
@@ -2242,6 +2312,9 @@ static void server_loop(Server* S) {
             }
             ++i;
         }
+        const size_t live = res.bytes() + workspace_bytes(S);
+        S->resident = live;
+        if (live > S->peak) S->peak = live;
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(5));
     }
 }
@@ -2324,6 +2397,14 @@ nmg_status nmg_poll(nmg_server* server, uint64_t ticket, int timeout_ms, nmg_sol
     S->by_ticket.erase(it);
     delete r;
     return st;
+}
+
+nmg_status nmg_server_memory(nmg_server* server, size_t* resident_bytes, size_t* peak_bytes) {
+    auto* S = reinterpret_cast<nmg::Server*>(server);
+    if (!S) return fail(NMG_ERR_INVALID, "NULL server");
+    if (resident_bytes) *resident_bytes = S->resident.load();
+    if (peak_bytes) *peak_bytes = S->peak.load();
+    return NMG_OK;
 }
 
 nmg_status nmg_server_destroy(nmg_server* server) {

@@ -120,6 +120,7 @@ struct Hierarchy {
     int64_t vgraph_nodes[3] = {0, 0, 0};
     // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
     unsigned* pbar = nullptr;
+    int wait_limit = 0;                  // > 0: iteration limit of the persistent grid-barrier wait
     unsigned* counters = nullptr;        // last-block tickets of the fused reductions
     int engine_choice[3] = {0, 0, 0};
     int fused[3] = {0, 0, 0};            // per-step engine: fused update/prolongation + residual kernels

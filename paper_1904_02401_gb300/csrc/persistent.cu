@@ -50,6 +50,7 @@ struct PArgs {
     int coarse_small;
     unsigned* bar;     // [0] arrivals, [1] generation
     int* abort;
+    int barrier_spins; // iteration limit of a grid-barrier wait
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -77,7 +78,7 @@ __device__ bool grid_sync(const PArgs& a) {
             } else {
                 int it = 0;
                 while (ld_acquire(&a.bar[1]) == gen) {
-                    if (++it > kBarrierSpins || ld_volatile(a.abort)) {
+                    if (++it > a.barrier_spins || ld_volatile(a.abort)) {
                         atomicExch(a.abort, 1);
                         ok = 0;
                         break;
@@ -328,6 +329,7 @@ cudaError_t launch_impl(const PArgs& a, size_t smem, cudaStream_t s) {
 cudaError_t launch_vcycle_persistent(Hierarchy* h, int prec, int nu1, int nu2, double omega, int weighting,
                                      unsigned* bar, int* abort, int small_patches) {
     PArgs a{};
+    a.barrier_spins = h->wait_limit > 0 ? h->wait_limit : kBarrierSpins;
     a.L = h->L;
     a.nu1 = nu1;
     a.nu2 = nu2;

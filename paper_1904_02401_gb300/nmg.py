@@ -121,6 +121,8 @@ _SIGS = {
     "nmg_server_destroy": [C.c_void_p],
     "nmg_server_set_workspaces": [C.c_void_p, C.c_int],
     "nmg_server_set_batching": [C.c_void_p, C.c_int],
+    "nmg_server_memory": [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+    "nmg_set_wait_limit": [_H, C.c_int],
     "nmg_vanka_correct_noalloc": [C.c_int, C.POINTER(C.c_int), C.c_int, _P, C.c_int64, _P, _P, C.c_double,
                                   C.c_int, C.c_int, _P],
 }
@@ -227,7 +229,8 @@ def nmg_profile_enable(h, enable) -> int:
 
 
 def nmg_profile_read(h, ms: C.c_double, launches: C.c_int64, bytes_per_launch: C.c_double) -> int:
-    return _lib.nmg_profile_read(h, C.byref(ms), C.byref(launches), C.byref(bytes_per_launch))
+    ref = lambda v: None if v is None else C.byref(v)
+    return _lib.nmg_profile_read(h, ref(ms), ref(launches), ref(bytes_per_launch))
 
 
 def nmg_vanka_correct_noalloc(dim, cells, precision, inv, inv_stride, d, x, omega, weighting, x_is_zero,
@@ -263,3 +266,12 @@ def nmg_server_set_batching(server, max_columns) -> int:
 
 def nmg_autotune_report(h, buf, length) -> int:
     return _lib.nmg_autotune_report(h, buf, length)
+
+
+def nmg_server_memory(server, resident: C.c_size_t, peak: C.c_size_t) -> int:
+    ref = lambda v: None if v is None else C.byref(v)
+    return _lib.nmg_server_memory(server, ref(resident), ref(peak))
+
+
+def nmg_set_wait_limit(h, spins) -> int:
+    return _lib.nmg_set_wait_limit(h, spins)

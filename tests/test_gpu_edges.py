@@ -120,3 +120,41 @@ def test_refused_descriptions(nmg):
     assert create(n=(6, 6), levels=2) == 0                     # coarsest level of 3 x 3 cells
     assert create(n=(12, 12), levels=2) == 0
     assert create(n=(64, 64), levels=1) == nmg.NMG_ERR_INVALID  # 65^2 x 3 unknowns on the coarsest level
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bounded_barrier_wait_times_out_and_recovers(nmg, prec):
+    """Every device-side wait is bounded.  With the persistent engine's grid-
+    barrier limit set to one poll, the barriers of a V-cycle run out: the
+    V-cycle and the solve return NMG_ERR_TIMEOUT without a fault, the flag is
+    cleared, and with the default limit restored the same hierarchy solves
+    again with exactly the result of a solve that never timed out."""
+    from paper_1904_02401_gb300.session import solve_opts
+    s = build_system(Problem(dim=2, n=(64, 64), levels=4, solid=(0, +1, 0.6)))
+    S = _session(s)
+    try:
+        b = torch.from_numpy(s.rhs).cuda()
+        o = solve_opts(precision=prec, engine=nmg.NMG_ENGINE_PERSISTENT, use_graph=0)
+        ref = torch.empty_like(b)
+        info = nmg.nmg_solve_info()
+        assert nmg.nmg_solve(S.handle, b, ref, o, info) == nmg.NMG_OK
+        its = info.iterations
+        dt = torch.float64 if prec == 0 else torch.float32
+        r = b.to(dt)
+        z = torch.zeros_like(r)
+        nmg.check(nmg.nmg_set_wait_limit(S.handle, 1))
+        assert nmg.nmg_vcycle(S.handle, o, r, z) == nmg.NMG_ERR_TIMEOUT
+        assert "aborted" in nmg.nmg_last_error()
+        x = torch.empty_like(b)
+        ot = solve_opts(precision=prec, engine=nmg.NMG_ENGINE_PERSISTENT, use_graph=0, maxit=40)
+        assert nmg.nmg_solve(S.handle, b, x, ot, info) == nmg.NMG_ERR_TIMEOUT
+        assert info.status == nmg.NMG_ERR_TIMEOUT
+        nmg.check(nmg.nmg_set_wait_limit(S.handle, 0))
+        assert nmg.nmg_solve(S.handle, b, x, o, info) == nmg.NMG_OK
+        assert info.iterations == its
+        assert torch.equal(x, ref)
+        # the other engines never used the limit
+        o2 = solve_opts(precision=prec, engine=nmg.NMG_ENGINE_KERNELS, use_graph=1)
+        assert nmg.nmg_solve(S.handle, b, x, o2, info) == nmg.NMG_OK
+    finally:
+        S.close()

@@ -132,6 +132,55 @@ def test_memory_budget_admission(pool):
         nmg.nmg_server_destroy(server)
 
 
+def test_budget_holds_while_fresh_hierarchies_allocate(pool):
+    """Two fresh hierarchies (no solve yet, so no Krylov bases) whose operators
+    and workspaces fit the budget together, but not once both have allocated
+    their FGMRES(30) bases: the server runs them one after the other, and the
+    resident bytes it reports never exceed the budget.  Both results equal
+    nmg_solve's bit for bit."""
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import Session, solve_opts
+    p = Problem(dim=2, n=(64, 64), levels=4, solid=(0, +1, 0.6), conv_seed=20)
+    s = build_system(p)
+    lv = [(l.row_ptr, l.col_idx, l.vals) for l in s.levels]
+    fresh = [Session(2, p.n, lv, s.dirichlet, precisions=1 << 1) for _ in range(2)]
+    alone = Session(2, p.n, lv, s.dirichlet, precisions=1 << 1)
+    try:
+        krylov = (2 * 30 + 1) * s.unknowns * 8
+        size0 = fresh[0].bytes()
+        budget = 2 * size0 + krylov   # room for one set of bases only
+        o = solve_opts(precision=1, engine=nmg.NMG_ENGINE_KERNELS, use_graph=1)
+        server = C.c_void_p()
+        nmg.check(nmg.nmg_server_create(budget, 8, server))
+        try:
+            bufs, tickets = [], []
+            for i, S in enumerate(fresh):
+                b = _rhs(s, 40 + i)
+                x = torch.zeros_like(b)
+                bufs.append((b, x))
+            torch.cuda.synchronize()
+            for S, (b, x) in zip(fresh, bufs):
+                t = C.c_uint64()
+                nmg.check(nmg.nmg_submit(server, S.handle, b, x, o, t))
+                tickets.append(t.value)
+            for t in tickets:
+                info = nmg.nmg_solve_info()
+                assert nmg.nmg_poll(server, t, 60000, info) == 0
+            resident, peak = C.c_size_t(), C.c_size_t()
+            nmg.check(nmg.nmg_server_memory(server, resident, peak))
+            assert size0 + krylov <= peak.value <= budget, (peak.value, budget)
+        finally:
+            nmg.nmg_server_destroy(server)
+        for S, (b, x) in zip(fresh, bufs):
+            assert S.bytes() == size0 + krylov                  # each now holds its bases
+            ref = torch.zeros_like(b)
+            alone.solve(b, ref, precision=1, engine=nmg.NMG_ENGINE_KERNELS, use_graph=1)
+            assert torch.equal(ref, x)
+    finally:
+        for S in fresh + [alone]:
+            S.close()
+
+
 def test_same_hierarchy_requests_overlap(pool):
     """With extra workspaces allowed, requests on one hierarchy run at the same
     time on workspace clones (own vectors and stream, shared matrices and

@@ -85,4 +85,6 @@ def test_invalid_arguments_refused_before_the_device(lib_path):
     assert nmg.nmg_solve_many(None, 1, buf, buf, o) == nmg.NMG_ERR_INVALID
     assert nmg.nmg_server_set_batching(None, 8) == nmg.NMG_ERR_INVALID
     assert nmg.nmg_server_set_workspaces(None, 1) == nmg.NMG_ERR_INVALID
+    assert nmg.nmg_server_memory(None, None, None) == nmg.NMG_ERR_INVALID
+    assert nmg.nmg_set_wait_limit(None, 1) == nmg.NMG_ERR_INVALID
     assert "NULL" in nmg.nmg_last_error() or "bad server" in nmg.nmg_last_error()
