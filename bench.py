@@ -7,7 +7,10 @@ rtol 1e-8 on the FP64 true residual) of the 2d 256x256 Q1 workload
 right-hand side is resident in HBM when the timed region starts; the L2 is
 flushed (a 256 MB write) before every timed solve, outside the per-solve
 events.  The same solve through the C ABI with host buffers gives "e2e"; the
-plain FP64 path on the same mesh is timed beside it.
+plain FP64 path on the same mesh is timed beside it, both solutions are
+compared with the FP64 oracle's, and compact records of the 3d 96^3 workload
+and of a serving sample follow on the same line (last, so that they stay in
+view at the end of the output).
 
 --impl reference times the FP64 CPU oracle (same method, same workload) on
 the host cores instead.  Under torchrun (N > 1) every rank solves its own
@@ -30,19 +33,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-8 rel. residual (mixed vs FP64 MG) and HBM GB/s; p50/p99 latency"
 WORKLOADS = {
-    "cfg2": ("2d 256x256 Q1 condensed-momentum Jacobian (198,147 unknowns), solid x>0.6, "
-             "7 MG levels, V(2,2) Vanka 2x2-cell patches (27 unknowns), FGMRES(30) rtol 1e-8"),
-    "cfg3": ("3d 32^3 Q1 condensed-momentum Jacobian (143,748 unknowns), solid z<0.25, "
-             "4 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
-    "cfg4": ("3d 96^3 Q1 condensed-momentum Jacobian (3,650,692 unknowns), solid z<0.25, "
-             "6 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
+    # the solid region is read on the coarsest mesh (every level resolves the same interface)
+    "cfg2": ("2d 256x256 Q1 condensed-momentum Jacobian (198,147 unknowns), solid x>0.6 read on the coarsest "
+             "4x4 mesh (interface x=0.5 on every level), 7 MG levels, V(2,2) Vanka 2x2-cell patches "
+             "(27 unknowns), FGMRES(30) rtol 1e-8"),
+    "cfg3": ("3d 32^3 Q1 condensed-momentum Jacobian (143,748 unknowns), solid z<0.25 read on the coarsest 4^3 "
+             "mesh (interface z=0.25), 4 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), "
+             "FGMRES(30) rtol 1e-8"),
+    "cfg4": ("3d 96^3 Q1 condensed-momentum Jacobian (3,650,692 unknowns), solid z<0.25 read on the coarsest 3^3 "
+             "mesh (interface z=1/3), 6 MG levels, V(2,2) Vanka 2x2x2-cell patches (108 unknowns), "
+             "FGMRES(30) rtol 1e-8"),
     # the ALE-extension solve (problem (3)) on the same meshes: d displacement components per node
     "ale2": ("2d 256x256 Q1 ALE-extension operator (vector Laplacian on the fluid, 132,098 unknowns), "
-             "solid x>0.6 fixed, 7 MG levels, V(2,2) Vanka 2x2-cell patches (18 unknowns), FGMRES(30) rtol 1e-8"),
+             "solid fixed (interface x=0.5), 7 MG levels, V(2,2) Vanka 2x2-cell patches (18 unknowns), "
+             "FGMRES(30) rtol 1e-8"),
     "ale3": ("3d 32^3 Q1 ALE-extension operator (vector Laplacian on the fluid, 107,811 unknowns), "
-             "solid z<0.25 fixed, 4 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), FGMRES(30) rtol 1e-8"),
+             "solid fixed (interface z=0.25), 4 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), "
+             "FGMRES(30) rtol 1e-8"),
     "ale4": ("3d 96^3 Q1 ALE-extension operator (vector Laplacian on the fluid, 2,738,019 unknowns), "
-             "solid z<0.25 fixed, 6 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), FGMRES(30) rtol 1e-8"),
+             "solid fixed (interface z=1/3), 6 MG levels, V(2,2) Vanka 2x2x2-cell patches (81 unknowns), "
+             "FGMRES(30) rtol 1e-8"),
+    # a mid-size 3d mesh whose finest patch inverses (645 MB FP32) exceed the L2, for kernel captures
+    "3d48": ("3d 48^3 Q1 condensed-momentum Jacobian (470,596 unknowns), solid z<0.25, 4 MG levels, V(2,2) "
+             "Vanka 2x2x2-cell patches (108 unknowns), FGMRES(30) rtol 1e-8"),
 }
 # the mesh each ALE workload shares with a condensed-momentum workload
 ALE_BASE = {"ale2": "cfg2", "ale3": "cfg3", "ale4": "cfg4"}
@@ -54,7 +67,11 @@ def load_workload(name):
     if name in ALE_BASE:
         p = config_problem(ALE_BASE[name])
         return build_ale_system(p), p.dim
-    p = config_problem(name)
+    if name == "3d48":
+        from gen import Problem
+        p = Problem(dim=3, n=(48, 48, 48), levels=4, solid=(2, -1, 0.25))
+    else:
+        p = config_problem(name)
     return build_system(p), p.dim + 1
 # DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
 # capture of the current kernel source (profiles/k_vanka_apply_*.md); a
@@ -65,6 +82,19 @@ PROFILED_TRAFFIC = {
 }
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
+
+
+def workload_config(sysm):
+    """The workload as both arms name it (no implementation details)."""
+    return {"workload": WORKLOAD_DESC, "unknowns": int(sysm.unknowns), "levels": int(sysm.problem.levels),
+            "rtol": 1e-8, "parallelism": "single GPU"}
+
+
+def sig(v, digits=4):
+    """Compact float for the output line (digits significant)."""
+    if v is None or isinstance(v, (int, bool, str)):
+        return v
+    return float(f"{v:.{digits}g}")
 
 
 def parse():
@@ -103,6 +133,9 @@ def parse():
                          "cudaProfilerStart and cudaProfilerStop, then exit (for an ncu launch list)")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS),
                     help="cfg2 is the measured workload; the others are for investigation")
+    ap.add_argument("--no-large", action="store_true", help="omit the compact 3d 96^3 record")
+    ap.add_argument("--no-serving-sample", action="store_true", help="omit the compact serving record")
+    ap.add_argument("--serving-sample", type=int, default=300, help="requests of the compact serving record")
     return ap.parse_args()
 
 
@@ -188,28 +221,42 @@ class ClockSampler:
 
 CHILD = r"""
 import json, os, sys, time
+import numpy as np
 sys.path.insert(0, {root!r})
 from bench import load_workload
 from oracle.solver import OracleSolver
 s, _ = load_workload({wl!r})
 o = OracleSolver(s.levels, s.dirichlet)
-times = []
+times, cpu = [], []
 info = None
 for _ in range({reps}):
-    t = time.perf_counter()
+    t, c = time.perf_counter(), time.process_time()
     x, info = o.solve(s.rhs, rtol=1e-8)
     times.append(time.perf_counter() - t)
-print(json.dumps({{"times": times, "iterations": info["iterations"], "rel_residual": info["rel_residual"],
-                   "setup_s": o.setup_seconds}}))
+    cpu.append(time.process_time() - c)
+if {save!r}:
+    np.save({save!r}, x)
+print(json.dumps({{"times": times, "cpu_times": cpu, "iterations": info["iterations"],
+                   "rel_residual": info["rel_residual"], "setup_s": o.setup_seconds}}))
 """
 
 
-def run_oracle(reps: int):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle(reps: int, threads: int = 1, save: str = ""):
+    """Runs the FP64 oracle solve reps times in a child process (no GPU) with
+    the BLAS/OpenMP thread pools capped at threads; save: .npy path for the
+    last solution."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT, wl=WORKLOAD, reps=reps)],
+    out = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT, wl=WORKLOAD, reps=reps, save=save)],
                          capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -221,17 +268,23 @@ def reference_arm(args):
     if rank != 0:
         return
     t0 = time.time()
-    res = run_oracle(args.warmup + args.steps)
+    sysm, _ = load_workload(WORKLOAD)
+    cores = host_cores()
+    res = run_oracle(args.warmup + args.steps, threads=cores)
     times = res["times"][args.warmup:]
     ms = 1000.0 * statistics.mean(times)
+    eff = sum(res["cpu_times"][args.warmup:]) / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "solver": "FP64 CPU oracle (numpy/scipy), same method"},
+        "config": workload_config(sysm),
+        "solver": "FP64 CPU oracle (numpy/scipy), same method",
         "iterations": res["iterations"], "rel_residual": res["rel_residual"],
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full oracle solves of the workload (setup excluded), 1 thread"},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "effective_cores": sig(eff, 3),
+                         "sample": f"{args.steps} full oracle solves of the workload (setup excluded), "
+                                   f"BLAS/OpenMP pools of {cores} threads"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.time() - t0,
     }
@@ -297,6 +350,8 @@ def gpu_arm(args):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
                 infos.append(info)
+                if profile:   # drain the library's event pool after every solve: every launch is counted
+                    nmg.check(nmg.nmg_profile_read(S.handle, None, None, None))
         prof = None
         if profile:
             import ctypes as C
@@ -355,6 +410,7 @@ def gpu_arm(args):
         dist.barrier()
     clk = clocks.stop()
 
+    xr = x.cpu().numpy()          # the mixed solution of the timed solves
     # the dominant kernel (finest-level Vanka apply) timed per launch with events on its launch
     # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
     ptimes, pinfos, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
@@ -362,8 +418,10 @@ def gpu_arm(args):
     _, _, sprof = timed_solves(args.precision, args.steps, 0, profile=3, engine=nmg.NMG_ENGINE_KERNELS)
     rep = C.create_string_buffer(32768)
     nmg.check(nmg.nmg_autotune_report(S.handle, rep, 32768))
+    tuned = json.loads(rep.value.decode())
     # plain FP64 path on the same mesh
     t64, i64, _ = timed_solves(nmg.NMG_PREC_FP64, args.steps, use_graph)
+    x64 = x.cpu().numpy()
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.from_numpy(sysm.rhs.copy()).pin_memory()
@@ -376,21 +434,7 @@ def gpu_arm(args):
         S.solve(bh, xh, precision=args.precision, use_graph=use_graph)
         e2e.append(1000.0 * (time.perf_counter() - t))
 
-    # set-up of the finest level for a new Jacobian (BSR already on the device): patch extraction
-    # and FP64 Gauss-Jordan inversion of every patch, stored in the prepared precisions
-    fin = sysm.fine
-    rp_d = torch.from_numpy(np.ascontiguousarray(fin.row_ptr, dtype=np.int64)).cuda()
-    ci_d = torch.from_numpy(np.ascontiguousarray(fin.col_idx, dtype=np.int32)).cuda()
-    v_d = torch.from_numpy(np.ascontiguousarray(fin.vals, dtype=np.float64)).cuda()
-    set_ms = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        nmg.check(nmg.nmg_set_jacobian(S.handle, sysm.problem.levels - 1, fin.nodes, ci_d.numel(), rp_d, ci_d, v_d, 1))
-        torch.cuda.synchronize()
-        set_ms.append(1000.0 * (time.perf_counter() - t))
-    del rp_d, ci_d, v_d
-
+    set_ms = _setup_ms(nmg, S, sysm)
     multi = _multi_rhs(args, S, sysm, stream, flush, use_graph) if args.rhs > 0 and args.precision != 0 else None
 
     ms = statistics.mean(times)
@@ -405,7 +449,7 @@ def gpu_arm(args):
     kms, klaunch, kbytes = prof
     vms, vcount, vbytes = vprof
     achieved = kbytes / (kms / klaunch * 1e-3) / 1e9 if klaunch else None
-    xr = x.cpu().numpy()
+    choice = tuned["choice"][args.precision]
     line = {
         "metric": METRIC,
         "value": ms_max,
@@ -419,23 +463,16 @@ def gpu_arm(args):
         "vs_baseline": None,
         "dtype": {0: "f64", 1: "f32+f64", 2: "bf16/f32+f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "unknowns": n, "levels": sysm.problem.levels,
-                   "vcycle_precision": {0: "fp64", 1: "fp32", 2: "bf16 factors"}[args.precision],
-                   "outer": "fp64 FGMRES(30)",
-                   "graphs": {0: "none (plain launches, host-stepped FGMRES)",
-                              1: "V-cycle graph, host-stepped FGMRES",
-                              2: "V-cycle inside one on-device graph loop per FGMRES restart cycle"}[use_graph],
-                   "device_loop": bool(infos[-1].device_loop),
-                   "l2": "flushed before every solve (256 MB write, outside the per-solve events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "iterations": infos[-1].iterations,
-        "engine": {1: "kernels", 2: "persistent", 3: "fused"}.get(infos[-1].engine, "?"),
-        "rel_residual": infos[-1].rel_residual,
-        "solves_per_s": job_throughput(world, ms_max),
-        "p50_ms": statistics.median(times),
-        "p99_ms": sorted(times)[max(0, int(0.99 * len(times)) - 1)],
-        "fp64_path": {"ms": statistics.mean(t64), "iterations": i64[-1].iterations,
-                      "speedup_of_mixed": statistics.mean(t64) / ms},
+        "config": dict(workload_config(sysm), parallelism="replicas" if world > 1 else "single GPU"),
+        "impl_detail": {"vcycle_precision": {0: "fp64", 1: "fp32", 2: "bf16 factors"}[args.precision],
+                        "outer": "fp64 FGMRES(30)",
+                        "graphs": {0: "none (plain launches, host-stepped FGMRES)",
+                                   1: "V-cycle graph, host-stepped FGMRES",
+                                   2: "V-cycle inside one on-device graph loop per restart cycle"}[use_graph],
+                        "device_loop": bool(infos[-1].device_loop),
+                        "engine": {1: "kernels", 2: "persistent", 3: "fused"}.get(infos[-1].engine, "?"),
+                        "autotuned": {k: choice[k] for k in ("tail_patches", "tile_patches", "fused")},
+                        "l2": "flushed before every solve (256 MB write, outside the per-solve events)"},
         "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 else "k_vanka_apply_ring") +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -443,34 +480,134 @@ def gpu_arm(args):
                      "traffic": PROFILED_TRAFFIC.get((WORKLOAD, args.precision)),
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
-                     "timed": f"{klaunch} launches over {args.steps} solves (events around each launch)"},
-        "spmv": _spmv_line(sprof, hbm, args.steps),
-        "setup": _setup_line(sysm, statistics.median(set_ms)),
-        "vcycle": {"ms": vms / vcount if vcount else None, "bytes": vbytes,
-                   "gbs": vbytes / (vms / vcount * 1e-3) / 1e9 if vcount else None,
-                   "engine": {1: "per-step kernels", 2: "persistent kernel",
-                              3: "per-step kernels, fused update/prolongation + residual"}.get(infos[-1].engine)},
-        "multi_rhs": multi,
-        "autotune": json.loads(rep.value.decode()),
+                     "timed": f"all {klaunch} launches of {args.steps} plain-launch solves (events around each)"},
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.launches for i in infos)),
         "clocks": clk,
+        "p50_ms": sig(statistics.median(times)),
+        "p99_ms": sig(sorted(times)[max(0, int(0.99 * len(times)) - 1)]),
+        "solves_per_s": sig(job_throughput(world, ms_max)),
     }
-    if not args.skip_cpu:
-        try:
-            res = run_oracle(1)
-            line["cpu_baseline"] = {"value": 1000.0 * res["times"][0], "unit": "ms", "cores": 1, "kind": "oracle",
-                                    "sample": "one full FP64 oracle solve of the same workload (setup excluded), "
-                                              "1 thread", "iterations": res["iterations"]}
-        except Exception as e:   # the GPU number stands without it
-            line["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
-    line["check"] = {"rel_residual_host": float(np.linalg.norm(sysm.rhs - _matvec(sysm, xr)) /
-                                                np.linalg.norm(sysm.rhs))}
+    oracle = _oracle_legs(args, sysm, xr, x64) if not args.skip_cpu else {}
+    if "cpu_baseline" in oracle:
+        line["cpu_baseline"] = oracle.pop("cpu_baseline")
+    # compact records, most important last
+    line["vcycle"] = {"us": sig(1000.0 * vms / vcount) if vcount else None,
+                      "GBps": sig(vbytes / (vms / vcount * 1e-3) / 1e9) if vcount else None,
+                      "algorithmic_MB": sig(vbytes / 1e6)}
+    line["setup"] = _setup_line(sysm, set_ms)
+    line["multi_rhs"] = multi
+    line["spmv"] = _spmv_line(sprof, hbm)
+    if world == 1 and not args.no_serving_sample:
+        line["serving"] = _serving_sample(args)
+    if world == 1 and not args.no_large and WORKLOAD == "cfg2":
+        S.close()                 # room for the 3d 96^3 hierarchy
+        line["cfg4"] = _large_record(args, hbm, flush)
+    line["rel_residual"] = sig(infos[-1].rel_residual, 3)
+    line["check"] = {"rel_residual_host": sig(float(np.linalg.norm(sysm.rhs - _matvec(sysm, xr)) /
+                                                    np.linalg.norm(sysm.rhs)), 3)}
+    line.update(oracle)
+    line["fp64_path"] = {"ms": sig(statistics.mean(t64)), "iterations": i64[-1].iterations,
+                         "speedup_of_mixed": sig(statistics.mean(t64) / ms)}
+    line["iterations"] = infos[-1].iterations
     print(json.dumps(line), flush=True)
     S.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _oracle_legs(args, sysm, x_mixed, x_fp64):
+    """The FP64 CPU oracle on the host: one solve with single-threaded BLAS /
+    OpenMP pools (its solution is the reference of rel_error_vs_oracle) and one
+    with pools of every host core (the cpu_baseline)."""
+    import tempfile
+
+    import numpy as np
+    out = {}
+    cores = host_cores()
+    try:
+        with tempfile.TemporaryDirectory() as tmp:
+            path = os.path.join(tmp, "x_oracle.npy")
+            one = run_oracle(1, threads=1, save=path)
+            xo = np.load(path)
+        allc = run_oracle(1, threads=cores)
+        eff = allc["cpu_times"][0] / allc["times"][0]
+        out["cpu_baseline"] = {"value": 1000.0 * allc["times"][0], "unit": "ms", "cores": cores, "kind": "oracle",
+                               "effective_cores": sig(eff, 3), "single_thread_ms": sig(1000.0 * one["times"][0]),
+                               "sample": "one full FP64 oracle solve of the same workload (setup excluded); "
+                                         f"BLAS/OpenMP pools of {cores} threads, and of 1 thread",
+                               "iterations": one["iterations"]}
+        nrm = np.linalg.norm(xo)
+        out["rel_error_vs_oracle"] = {
+            "mixed": sig(float(np.linalg.norm(x_mixed - xo) / nrm), 3),
+            "fp64": sig(float(np.linalg.norm(x_fp64 - xo) / nrm), 3),
+            "oracle_iterations": one["iterations"]}
+    except Exception as e:   # the GPU numbers stand without it
+        out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    return out
+
+
+def _large_record(args, hbm, flush):
+    """The 3d 96^3 workload (3,650,692 unknowns, 6 levels) measured in the same
+    run: time to 1e-8 with FP32 and BF16 patch inverses and with the plain FP64
+    path (graphs, on-device restart loops, L2 flushed before each solve), the
+    finest Vanka apply and SpMV against the HBM copy rate, and the set-up."""
+    import numpy as np
+    import torch
+    from gen import build_system, config_problem
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import Session
+
+    t0 = time.time()
+    sysm = build_system(config_problem("cfg4"))
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    S = Session(sysm.problem.dim, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels],
+                sysm.dirichlet, stream=stream.cuda_stream)
+    b = torch.from_numpy(sysm.rhs).cuda()
+    x = torch.empty_like(b)
+
+    def solves(prec, k, graph=2, profile=0, engine=nmg.NMG_ENGINE_AUTO):
+        ts, info = [], None
+        if profile:
+            nmg.check(nmg.nmg_profile_enable(S.handle, profile))
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = S.solve(b, x, precision=prec, use_graph=graph, engine=engine)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                if profile:
+                    nmg.check(nmg.nmg_profile_read(S.handle, None, None, None))
+        prof = None
+        if profile:
+            import ctypes as C
+            ms, cnt, bpl = C.c_double(), C.c_int64(), C.c_double()
+            nmg.check(nmg.nmg_profile_read(S.handle, ms, cnt, bpl))
+            nmg.check(nmg.nmg_profile_enable(S.handle, 0))
+            prof = bpl.value / (ms.value / cnt.value * 1e-3) / 1e9 if cnt.value else None
+        return statistics.mean(ts), info, prof
+
+    rec = {"unknowns": int(sysm.unknowns)}
+    for name, prec in (("fp32", 1), ("bf16", 2), ("fp64_path", 0)):
+        solves(prec, 2)                                  # warm-up (autotune, graph capture)
+        ms, info, _ = solves(prec, 3 if prec else 2)
+        rec[name] = {"ms": sig(ms), "iterations": info.iterations, "rel_residual": sig(info.rel_residual, 3)}
+    rec["speedup_fp32"] = sig(rec["fp64_path"]["ms"] / rec["fp32"]["ms"], 3)
+    rec["speedup_bf16"] = sig(rec["fp64_path"]["ms"] / rec["bf16"]["ms"], 3)
+    _, _, apply_gbs = solves(1, 1, graph=0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
+    _, _, spmv_gbs = solves(1, 1, graph=0, profile=3, engine=nmg.NMG_ENGINE_KERNELS)
+    rec["apply_fp32_frac"] = sig(apply_gbs / hbm, 3) if apply_gbs else None
+    rec["spmv_fp32_frac"] = sig(spmv_gbs / hbm, 3) if spmv_gbs else None
+    rec["setup_ms"] = sig(_setup_ms(nmg, S, sysm))
+    rec["host_gen_s"] = sig(gen_s, 3)
+    S.close()
+    del sysm
+    return rec
 
 
 def _multi_rhs(args, S, sysm, stream, flush, use_graph):
@@ -535,15 +672,13 @@ def _multi_rhs(args, S, sysm, stream, flush, use_graph):
     vs = lambda: nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=1), R[0], z1))
     timed(vs, 2)
     v_single = statistics.mean(t for t, _ in timed(vs, 10))
-    return {"what": f"{K} right-hand sides, one hierarchy: nmg_solve_many (lockstep FGMRES, one multi-vector "
-                    f"V-cycle per step for all columns) vs {K} nmg_solve calls; L2 flushed before each timed call",
-            "columns": K, "ms": ms_many, "ms_per_column": ms_many / K, "solves_per_s": 1000.0 * K / ms_many,
-            "single_ms_per_column": ms_single / K, "speedup": ms_single / ms_many,
-            "iterations": [i.iterations for i in infos], "single_iterations": sruns[-1][1],
-            "vcycle_ms_per_column": v_many / K, "single_vcycle_ms": v_single, "vcycle_speedup": v_single * K / v_many}
+    its = [i.iterations for i in infos]
+    return {"columns": K, "ms_per_column": sig(ms_many / K), "single_ms_per_column": sig(ms_single / K),
+            "speedup": sig(ms_single / ms_many, 3), "iterations_equal": its == list(sruns[-1][1]),
+            "vcycle_us_per_column": sig(1000.0 * v_many / K), "single_vcycle_us": sig(1000.0 * v_single)}
 
 
-def _spmv_line(prof, hbm, steps):
+def _spmv_line(prof, hbm):
     """The finest-level residual product (block SpMV), timed per launch with
     events on its stream inside plain-launch solves: algorithmic bytes (Q1
     blocks once, x, b and r once) over the mean launch time."""
@@ -551,9 +686,8 @@ def _spmv_line(prof, hbm, steps):
     if not cnt:
         return None
     gbs = nbytes / (ms / cnt * 1e-3) / 1e9
-    return {"kernel": "k_spmv / k_spmv_rows (finest-level residual product)", "bound": "hbm", "achieved": gbs,
-            "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "launch_ms": ms / cnt, "bytes_per_launch": nbytes,
-            "timed": f"{cnt} launches over {steps} solves (events around each launch)"}
+    return {"GBps": sig(gbs), "frac": sig(gbs / hbm, 3),
+            "us": sig(1000.0 * ms / cnt), "MB": sig(nbytes / 1e6), "launches": cnt}
 
 
 # FP64 peak of one GB300 derived from its units and clock: 152 SMs x 2 FP64 FMA
@@ -561,20 +695,37 @@ def _spmv_line(prof, hbm, steps):
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 
 
+def _setup_ms(nmg, S, sysm):
+    """Median of 3 re-factorisations of the finest level through
+    nmg_set_jacobian from device buffers (a new Jacobian: stencil copy, FP32
+    copy, patch extraction and FP64 inversion of every patch)."""
+    import numpy as np
+    import torch
+    fin = sysm.fine
+    rp_d = torch.from_numpy(np.ascontiguousarray(fin.row_ptr, dtype=np.int64)).cuda()
+    ci_d = torch.from_numpy(np.ascontiguousarray(fin.col_idx, dtype=np.int32)).cuda()
+    v_d = torch.from_numpy(np.ascontiguousarray(fin.vals, dtype=np.float64)).cuda()
+    out = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        nmg.check(nmg.nmg_set_jacobian(S.handle, sysm.problem.levels - 1, fin.nodes, ci_d.numel(), rp_d, ci_d, v_d, 1))
+        torch.cuda.synchronize()
+        out.append(1000.0 * (time.perf_counter() - t))
+    return statistics.median(out)
+
+
 def _setup_line(sysm, ms):
-    """Re-factorisation of the finest level (nmg_set_jacobian from device
-    buffers): Gauss-Jordan inversion of every n_p x n_p patch, n_p^3 FP64 FMAs
-    each, against the FP64 ALU peak."""
+    """Re-factorisation of the finest level: Gauss-Jordan inversion of every
+    n_p x n_p patch, n_p^3 FP64 FMAs each, against the FP64 ALU peak."""
     d = sysm.problem.dim
     patches = 1
     for nk in sysm.problem.n:
         patches *= nk // 2
     n_p = 3 ** d * int(sysm.fine.vals.shape[1])
     gflops = 2.0 * patches * n_p ** 3 / (ms * 1e-3) / 1e9
-    return {"what": "nmg_set_jacobian of the finest level: stencil copy, FP32 copy, patch extraction and FP64 "
-                    "Gauss-Jordan inversion of every patch (median of 3)", "ms": ms, "patches": patches, "n_p": n_p,
-            "bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-            "frac": gflops / FP64_PEAK_GFLOPS}
+    return {"ms": sig(ms), "patches": patches, "n_p": n_p, "GFLOPs_fp64": sig(gflops),
+            "frac_fp64_alu": sig(gflops / FP64_PEAK_GFLOPS, 3)}
 
 
 def _matvec(sysm, x):
@@ -585,18 +736,16 @@ def _matvec(sysm, x):
     return A @ x
 
 
-def serving_arm(args):
+def _serve(args, sizes, seeds, n_requests, n_burst):
     """Continuous-batching serving of condensed-momentum solves.
 
-    Meshes uniform over 2d {64^2, 128^2, 256^2, 512^2} and 3d {16^3, 32^3,
-    64^3} (50/50 between 2d and 3d); each mesh size has a pool of two resident
-    hierarchies (coefficient seeds 10 and 12); request i draws its mesh and
-    hierarchy from numpy default_rng(2) and its right-hand side from the CUDA
-    generator seeded 11 + 2 i.  Arrivals are a Poisson stream (seed 2) at 80%
-    of the saturated throughput measured first on a burst of the same mix.
-    One server (16 slots, 150 GB) serves the warm-up, the burst and the timed
-    stream, so the workspaces it adds for concurrent requests on one
-    hierarchy are made during the warm-up.
+    Each mesh size of sizes ((dim, n) pairs) has a pool of resident
+    hierarchies, one per coefficient seed in seeds; request i draws its mesh
+    and hierarchy from numpy default_rng(2) (2d and 3d 50/50) and its
+    right-hand side from the CUDA generator seeded 11 + 2 i.  Arrivals are a
+    Poisson stream (seed 2) at 80% of the saturated throughput measured first
+    on a burst of n_burst requests of the same mix.  One server (16 slots,
+    150 GB) serves the warm-up, the burst and the timed stream.
     """
     import ctypes as C
 
@@ -608,12 +757,6 @@ def serving_arm(args):
     from paper_1904_02401_gb300.session import Session, solve_opts
 
     torch.cuda.set_device(0)
-    sizes = [(2, 64), (2, 128), (2, 256), (2, 512), (3, 16), (3, 32), (3, 64)]
-    seeds = (10, 12)
-    if args.mesh:
-        d, nn = args.mesh.split(":")
-        sizes = [(int(d[0]), int(nn))]
-        seeds = (10,)
     pool = []
     t0 = time.time()
     for dim, n in sizes:
@@ -632,12 +775,13 @@ def serving_arm(args):
     opts = solve_opts(precision=nmg.NMG_PREC_FP32, engine=nmg.NMG_ENGINE_KERNELS,
                       use_graph=0 if args.no_graph else args.graph)
     budget = 150 * 10**9
+    both = len({d for d, _ in sizes}) > 1
 
     def make_requests(count, seed0):
         out = []
         for i in range(count):
             d2 = rng.random() < 0.5
-            cands = [k for k, (dim, n, S, m) in enumerate(pool) if (dim == 2) == d2 or args.mesh]
+            cands = [k for k, (dim, n, S, m) in enumerate(pool) if (dim == 2) == d2 or not both]
             k = int(rng.choice(cands))
             dim, n, S, mask = pool[k]
             g = torch.Generator(device="cuda").manual_seed(seed0 + 2 * i)
@@ -673,19 +817,38 @@ def serving_arm(args):
         wall = time.perf_counter() - start
         return wall, lat, its, bad
 
-    burst = make_requests(200, 1_000_011)
+    burst = make_requests(n_burst, 1_000_011)
     run(burst[:20], 0)                       # warm-up (graphs captured, engines resolved)
     wall_b, _, _, _ = run(burst, 0)
     saturated = len(burst) / wall_b
     del burst
-    reqs = make_requests(args.requests, 11)
+    reqs = make_requests(n_requests, 11)
     rate = 0.8 * saturated
     wall, lat, its, bad = run(reqs, rate)
     nmg.nmg_server_destroy(server)
+    for _, _, S, _ in pool:
+        S.close()
     lat_sorted = sorted(lat)
+    return {"requests": len(reqs), "hierarchies": len(pool), "p50_ms": statistics.median(lat),
+            "p99_ms": lat_sorted[max(0, int(0.99 * len(lat)) - 1)], "solves_per_s": len(reqs) / wall,
+            "arrival_rate_per_s": rate, "saturated_solves_per_s": saturated, "failed": bad,
+            "mean_iterations": statistics.mean(its), "setup_s": setup_s}
+
+
+SERVING_SIZES = [(2, 64), (2, 128), (2, 256), (2, 512), (3, 16), (3, 32), (3, 64)]
+
+
+def serving_arm(args):
+    """The serving workload as its own bench line (--serving): 2000 requests
+    over two resident hierarchies per mesh size (or one mesh, --mesh)."""
+    sizes, seeds = SERVING_SIZES, (10, 12)
+    if args.mesh:
+        d, nn = args.mesh.split(":")
+        sizes, seeds = [(int(d[0]), int(nn))], (10,)
+    r = _serve(args, sizes, seeds, args.requests, 200)
     line = {
-        "metric": METRIC, "value": statistics.median(lat), "unit": "ms (p50 submit-to-completion latency)",
-        "n_gpus": 1, "steps": len(reqs), "warmup": 20, "higher_is_better": False, "scaling": "weak",
+        "metric": METRIC, "value": r["p50_ms"], "unit": "ms (p50 submit-to-completion latency)",
+        "n_gpus": 1, "steps": r["requests"], "warmup": 20, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": ("serving: Poisson stream of condensed-momentum solves, 2d 64^2-512^2 and 3d "
                                 "16^3-64^3 (50/50), 14 resident hierarchies, FP32 V-cycle / FP64 FGMRES(30), "
@@ -695,14 +858,23 @@ def serving_arm(args):
                                 "rtol 1e-8, memory budget 150 GB, 16 slots"),
                    "extra_workspaces_per_hierarchy": args.workspaces,
                    "batched_columns": args.batch,
-                   "arrival_rate_per_s": rate, "saturated_solves_per_s": saturated},
-        "p50_ms": statistics.median(lat), "p99_ms": lat_sorted[max(0, int(0.99 * len(lat)) - 1)],
-        "solves_per_s": len(reqs) / wall, "failed": bad, "mean_iterations": statistics.mean(its),
-        "setup_s": setup_s,
+                   "arrival_rate_per_s": r["arrival_rate_per_s"],
+                   "saturated_solves_per_s": r["saturated_solves_per_s"]},
+        "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "solves_per_s": r["solves_per_s"], "failed": r["failed"],
+        "mean_iterations": r["mean_iterations"], "setup_s": r["setup_s"],
     }
     print(json.dumps(line), flush=True)
-    for _, _, S, _ in pool:
-        S.close()
+
+
+def _serving_sample(args):
+    """A bounded sample of the serving workload for the main line: every mesh
+    size of the serving mix with one resident hierarchy each, a burst of 100
+    requests for the saturated rate, then args.serving_sample requests at 80%
+    of it."""
+    r = _serve(args, SERVING_SIZES, (10,), args.serving_sample, 100)
+    return {"requests": r["requests"], "hierarchies": r["hierarchies"], "p50_ms": sig(r["p50_ms"]), "p99_ms": sig(r["p99_ms"]),
+            "solves_per_s": sig(r["solves_per_s"]), "saturated_per_s": sig(r["saturated_solves_per_s"]),
+            "failed": r["failed"]}
 
 
 def main():
