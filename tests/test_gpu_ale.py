@@ -173,12 +173,16 @@ def test_ale_transfers_and_coarse(nmg, built, sessions, case, prec):
 def test_ale_solve_fp64_matches_oracle(nmg, built, sessions, case, use_graph):
     s, h = built[case]
     S = sessions[case]
-    xo, info_o = fgmres(h.fine.A.matvec, h.vcycle, s.rhs, rtol=1e-8)
+    hist = []
+    xo, info_o = fgmres(h.fine.A.matvec, h.vcycle, s.rhs, rtol=1e-8, history=hist)
     b = cu(s.rhs, np.float64)
     x = torch.empty_like(b)
     info = S.solve(b, x, precision=0, use_graph=use_graph)
     assert info.status == 0
-    assert abs(info.iterations - info_o["iterations"]) <= 1, (info.iterations, info_o)
+    # equal counts; one either way only when the final estimate lies within 1 % of rtol
+    near = any(1e-8 / 1.01 <= v <= 1e-8 * 1.01 for v in hist[-2:])
+    assert info.iterations == info_o["iterations"] or (near and abs(info.iterations - info_o["iterations"]) <= 1), \
+        (info.iterations, info_o)
     xg = host(x)
     assert rel(xg, xo) <= 1e-8
     assert np.linalg.norm(s.rhs - h.fine.A.matvec(xg)) / np.linalg.norm(s.rhs) <= 1e-8
