@@ -413,8 +413,12 @@ def gpu_arm(args):
     xr = x.cpu().numpy()          # the mixed solution of the timed solves
     # the dominant kernel (finest-level Vanka apply) timed per launch with events on its launch
     # stream (plain launches of the per-step engine), and whole V-cycles in the timed configuration
-    prof = cold_launches(nmg, S, sysm, stream, flush, args.precision, 2, args.steps)
-    sprof = cold_launches(nmg, S, sysm, stream, flush, args.precision, 3, args.steps)
+    # in the solve: every launch of plain-launch solves (engine KERNELS), events around each launch
+    _, _, prof = timed_solves(args.precision, args.steps, 0, profile=2, engine=nmg.NMG_ENGINE_KERNELS)
+    _, _, sprof = timed_solves(args.precision, args.steps, 0, profile=3, engine=nmg.NMG_ENGINE_KERNELS)
+    # alone: one launch at a time after an L2-evicting write
+    cold = cold_launches(nmg, S, sysm, stream, flush, args.precision, 2, args.steps)
+    scold = cold_launches(nmg, S, sysm, stream, flush, args.precision, 3, args.steps)
     _, _, vprof = timed_solves(args.precision, args.steps, min(use_graph, 1), profile=1)
     rep = C.create_string_buffer(32768)
     nmg.check(nmg.nmg_autotune_report(S.handle, rep, 32768))
@@ -480,8 +484,9 @@ def gpu_arm(args):
                      "traffic": PROFILED_TRAFFIC.get((WORKLOAD, args.precision)),
                      "peak_kind": peak_kind, "launch_ms": kms / klaunch if klaunch else None,
                      "bytes_per_launch": kbytes,
-                     "timed": f"{klaunch} launches of the finest level, each after a 256 MB write (cold L2), "
-                              "events around each on its stream"},
+                     "timed": f"all {klaunch} launches of {args.steps} plain-launch solves, events around each on "
+                              "its stream (the level's data partly L2-resident between smoothing steps)",
+                     "cold": _cold_line(cold, hbm)},
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.launches for i in infos)),
@@ -499,7 +504,7 @@ def gpu_arm(args):
                       "algorithmic_MB": sig(vbytes / 1e6)}
     line["setup"] = _setup_line(sysm, set_ms)
     line["multi_rhs"] = multi
-    line["spmv"] = _spmv_line(sprof, hbm)
+    line["spmv"] = dict(_spmv_line(sprof, hbm) or {}, cold=_cold_line(scold, hbm))
     if world == 1 and not args.no_serving_sample:
         line["serving"] = _serving_sample(args)
     if world == 1 and not args.no_large and WORKLOAD == "cfg2":
@@ -712,11 +717,19 @@ def _multi_rhs(args, S, sysm, stream, flush, use_graph):
             "vcycle_us_per_column": sig(1000.0 * v_many / K), "single_vcycle_us": sig(1000.0 * v_single)}
 
 
+def _cold_line(prof, hbm):
+    """Rate of launches timed alone after an L2-evicting write (cold_launches)."""
+    ms, cnt, nbytes = prof
+    if not cnt:
+        return None
+    gbs = nbytes / (ms / cnt * 1e-3) / 1e9
+    return {"us": sig(1000.0 * ms / cnt), "GBps": sig(gbs), "frac": sig(gbs / hbm, 3)}
+
+
 def _spmv_line(prof, hbm):
     """The finest-level residual product (block SpMV), timed per launch with
-    events on its stream, each launch after an L2-evicting write
-    (cold_launches): algorithmic bytes (Q1 blocks once, x, b and r once) over
-    the mean launch time."""
+    events on its stream inside plain-launch solves: algorithmic bytes (Q1
+    blocks once, x, b and r once) over the mean launch time."""
     ms, cnt, nbytes = prof
     if not cnt:
         return None
