@@ -22,13 +22,14 @@ import numpy as np
 import scipy.linalg as sla
 
 from .bsr import BlockMatrix
-from .mesh import coarse_mask, patch_dofs
+from .mesh import coarse_cell_mask, coarse_mask, patch_dofs
 from .transfer import prolongation
-from .vanka import overlap_weights, patch_inverses, patch_matrices, vanka_step
+from .vanka import (group_weights, overlap_weights, patch_groups, patch_inverses, patch_matrices, vanka_step,
+                    vanka_step_groups)
 
 
 class Level:
-    def __init__(self, cells, row_ptr, col_idx, vals, mask, smooth: bool, weighting: str):
+    def __init__(self, cells, row_ptr, col_idx, vals, mask, smooth: bool, weighting: str, large_mask=None):
         self.cells = tuple(int(c) for c in cells)
         self.A = BlockMatrix(row_ptr, col_idx, vals)
         self.ncomp = self.A.ncomp
@@ -37,7 +38,14 @@ class Level:
         self.dofs = None
         self.Ainv = None
         self.weight = None
-        if smooth:
+        self.groups = None       # patches of two sizes: [(dofs, inverses)] per size
+        if smooth and large_mask is not None and np.asarray(large_mask).any():
+            self.groups = patch_groups(self.A, self.cells, large_mask)
+            self.weight = group_weights(self.groups, self.A.size, weighting)
+            if len(self.groups) == 1:    # no 4-aligned block fits the region on this level
+                self.dofs, self.Ainv = self.groups[0]
+                self.groups = None
+        elif smooth:
             self.dofs = patch_dofs(self.cells, self.ncomp)
             self.Ainv = patch_inverses(patch_matrices(self.A, self.cells))
             self.weight = overlap_weights(self.dofs, self.A.size, weighting)
@@ -46,7 +54,10 @@ class Level:
 class Hierarchy:
     """Levels coarsest first; ``levels`` holds objects with cells/row_ptr/col_idx/vals."""
 
-    def __init__(self, levels, fine_mask, nu1=2, nu2=2, omega=0.8, weighting="average"):
+    def __init__(self, levels, fine_mask, nu1=2, nu2=2, omega=0.8, weighting="average", large_cells=None):
+        """large_cells: None, or bool per finest-level cell (array order (z,) y, x)
+        flagging the region of large patches (Section 5.5.1); a coarse cell is
+        flagged iff all its children are."""
         self.nu1, self.nu2, self.omega = int(nu1), int(nu2), float(omega)
         L = len(levels)
         masks = [None] * L
@@ -57,10 +68,15 @@ class Hierarchy:
                 if a != 2 * b:
                     raise ValueError("levels must halve the cell count per direction")
             masks[lev - 1] = coarse_mask(masks[lev], levels[lev].cells, nc)
+        large = [None] * L
+        if large_cells is not None:
+            large[L - 1] = np.asarray(large_cells, dtype=bool)
+            for lev in range(L - 1, 0, -1):
+                large[lev - 1] = coarse_cell_mask(large[lev])
         self.levels = []
         for lev, m in enumerate(levels):
             self.levels.append(Level(m.cells, m.row_ptr, m.col_idx, m.vals, masks[lev], smooth=lev > 0,
-                                     weighting=weighting))
+                                     weighting=weighting, large_mask=large[lev]))
         for lev in range(1, L):
             self.levels[lev].P = prolongation(self.levels[lev - 1].cells, nc)
         self.coarse_lu = sla.lu_factor(self.levels[0].A.dense())
@@ -72,7 +88,10 @@ class Hierarchy:
     def smooth(self, lev: int, b, x, steps: int):
         L = self.levels[lev]
         for _ in range(steps):
-            x = vanka_step(L.A, L.Ainv, L.dofs, b, x, self.omega, L.weight)
+            if L.groups is not None:
+                x = vanka_step_groups(L.A, L.groups, b, x, self.omega, L.weight)
+            else:
+                x = vanka_step(L.A, L.Ainv, L.dofs, b, x, self.omega, L.weight)
         return x
 
     def restrict_residual(self, lev: int, b, x):

@@ -68,6 +68,8 @@ def with_stored_inverses(hierarchy, fmt: str):
         c = copy.copy(L)
         if L.Ainv is not None:
             c.Ainv = round_storage(L.Ainv, fmt)
+        if getattr(L, "groups", None) is not None:
+            c.groups = [(dofs, round_storage(inv, fmt)) for dofs, inv in L.groups]
         h.levels.append(c)
     return h
 
@@ -106,6 +108,9 @@ def with_fp32_arithmetic(hierarchy, fmt: str):
         c.A = _Float32Matrix(L.A)
         if L.Ainv is not None:
             c.Ainv = round_storage(L.Ainv, fmt).astype(np.float32)
+        if getattr(L, "groups", None) is not None:
+            c.groups = [(dofs, round_storage(inv, fmt).astype(np.float32)) for dofs, inv in L.groups]
+        if L.weight is not None:
             c.weight = L.weight.astype(np.float32)
         if L.P is not None:
             c.P = L.P.astype(np.float32)

@@ -19,12 +19,17 @@ from __future__ import annotations
 
 import numpy as np
 
-from .mesh import patch_nodes
+from .mesh import block_nodes, patch_blocks, patch_nodes
 
 
 def patch_matrices(A, cells) -> np.ndarray:
     """A_i = R_i A R_i^T for every patch, shape (patches, n_p, n_p), n_p = 3^d n_c."""
-    nodes = patch_nodes(cells)                       # (P, m), m = 3^d
+    return node_block_matrices(A, patch_nodes(cells))
+
+
+def node_block_matrices(A, nodes) -> np.ndarray:
+    """R_i A R_i^T for patches given by their node lists nodes (P, m):
+    shape (P, m n_c, m n_c), unknowns node-major."""
     P, m = nodes.shape
     nc = A.ncomp
     blocks = A.block_lookup(nodes[:, :, None], nodes[:, None, :])   # (P, m, m, nc, nc)
@@ -53,4 +58,44 @@ def vanka_step(A, Ainv, dofs, b, x, omega, weight):
     local = np.einsum("pij,pj->pi", Ainv, d[dofs])
     corr = np.zeros_like(x)
     np.add.at(corr, dofs, local)
+    return x + omega * weight * corr
+
+
+def patch_groups(A, cells, large_mask=None):
+    """The patches of a level with their exact inverses, grouped by size:
+    a list of (dofs (P, n_p), inverses (P, n_p, n_p)), small patches (2^d
+    cells) first, then large ones (4^d cells) where large_mask flags whole
+    4-aligned blocks (mesh.patch_blocks)."""
+    nc = A.ncomp
+    out = []
+    blocks = patch_blocks(cells, large_mask)
+    for size in (2, 4):
+        sel = [o for o, s in blocks if s == size]
+        if not sel:
+            continue
+        nodes = np.stack([block_nodes(cells, o, size) for o in sel])
+        dofs = (nodes[:, :, None] * nc + np.arange(nc)[None, None, :]).reshape(nodes.shape[0], -1)
+        out.append((dofs, patch_inverses(node_block_matrices(A, nodes))))
+    return out
+
+
+def group_weights(groups, size: int, weighting: str = "average") -> np.ndarray:
+    """overlap_weights over the patches of every group."""
+    if weighting == "sum":
+        return np.ones(size)
+    if weighting != "average":
+        raise ValueError(weighting)
+    m = np.zeros(size)
+    for dofs, _ in groups:
+        np.add.at(m, dofs, 1.0)
+    return 1.0 / m
+
+
+def vanka_step_groups(A, groups, b, x, omega, weight):
+    """Eq. (vanka) with patches of several sizes: the corrections of every
+    patch of every group summed, then weighted and damped."""
+    d = b - A.matvec(x)
+    corr = np.zeros_like(x)
+    for dofs, Ainv in groups:
+        np.add.at(corr, dofs, np.einsum("pij,pj->pi", Ainv, d[dofs]))
     return x + omega * weight * corr
