@@ -439,6 +439,8 @@ def gpu_arm(args):
         e2e.append(1000.0 * (time.perf_counter() - t))
 
     set_ms = _setup_ms(nmg, S, sysm)
+    # (the layout study runs before the multi-vector solves: a layout is set before those)
+    sizes = _patch_sizes(args, S, sysm, stream, flush, use_graph) if ncomp == sysm.problem.dim + 1 else None
     multi = _multi_rhs(args, S, sysm, stream, flush, use_graph) if args.rhs > 0 and args.precision != 0 else None
 
     ms = statistics.mean(times)
@@ -504,6 +506,7 @@ def gpu_arm(args):
                       "algorithmic_MB": sig(vbytes / 1e6)}
     line["setup"] = _setup_line(sysm, set_ms)
     line["multi_rhs"] = multi
+    line["patch_sizes"] = sizes
     line["spmv"] = dict(_spmv_line(sprof, hbm) or {}, cold=_cold_line(scold, hbm))
     if world == 1 and not args.no_serving_sample:
         line["serving"] = _serving_sample(args)
@@ -647,6 +650,48 @@ def cold_launches(nmg, S, sysm, stream, flush, prec, mode, reps):
     nmg.check(nmg.nmg_profile_read(S.handle, ms, cnt, bpl))
     nmg.check(nmg.nmg_profile_enable(S.handle, 0))
     return ms.value, cnt.value, bpl.value
+
+
+def _patch_sizes(args, S, sysm, stream, flush, use_graph):
+    """The Vanka patch-size study of Section 5.5.1 on this workload: small
+    patches (2^d cells) everywhere, large ones (4^d cells) on the solid, on the
+    fluid, and everywhere (F/S: unknowns per patch in the fluid / the solid).
+    Per layout: FGMRES iterations, time per solve with the per-step-kernel
+    engine (the only one for two patch sizes; L2 flushed before each) and the
+    re-factorisation of every level in that layout (nmg_set_large_patches on
+    the resident hierarchy)."""
+    import numpy as np
+    import torch
+    from gen.q1fsi import solid_cells
+    p = sysm.problem
+    small, large = 3 ** p.dim * p.ncomp, 5 ** p.dim * p.ncomp
+    solid = solid_cells(p, p.n)
+    layouts = [(f"F{small}/S{small}", None), (f"F{small}/S{large}", solid), (f"F{large}/S{small}", ~solid),
+               (f"F{large}/S{large}", np.ones_like(solid))]
+    b = torch.from_numpy(sysm.rhs).cuda()
+    x = torch.empty_like(b)
+    out = {}
+    for name, region in layouts:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        S.set_large_patches(region)
+        torch.cuda.synchronize()
+        set_ms = 1000.0 * (time.perf_counter() - t)
+        ts, info = [], None
+        with torch.cuda.stream(stream):
+            for k in range(2 + max(3, args.steps // 4)):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = S.solve(b, x, precision=args.precision, use_graph=use_graph, engine=1)   # per-step kernels
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 2:
+                    ts.append(e0.elapsed_time(e1))
+        out[name] = {"iterations": info.iterations, "ms": sig(statistics.mean(ts)), "refactor_ms": sig(set_ms, 3),
+                     "ok": info.status == 0}
+    S.set_large_patches(None)
+    return out
 
 
 def _multi_rhs(args, S, sysm, stream, flush, use_graph):

@@ -362,11 +362,39 @@ nmg_status nmg_vcycle(nmg_hierarchy* h, const nmg_solve_opts* opts, const void* 
  * nrhs < 1 or precision FP64. */
 nmg_status nmg_vcycle_many(nmg_hierarchy* h, const nmg_solve_opts* opts, int nrhs, const void* r, void* z);
 
+/* Vanka patches of two sizes (Section 5.5.1): over the cells flagged in
+ * cell_mask (host, one byte per finest-level cell, x fastest; non-zero =
+ * flagged) the smoother uses large patches, blocks of 4^dim cells (5^dim
+ * nodes: 75 unknowns in 2d, 500 in 3d for ncomp = dim + 1), on every
+ * 4-aligned block whose cells are all flagged; every other cell keeps the
+ * small patch of its 2-aligned block of 2^dim cells.  A coarser cell is
+ * flagged when all its children are.  Each unknown's summed correction is
+ * weighted by the number of patches of either size containing it (with
+ * NMG_WEIGHT_AVERAGE).  cell_mask NULL restores small patches everywhere.
+ * Levels already set are factored again in the new layout (large patches by
+ * FP64 Gauss-Jordan with partial pivoting: in shared memory in 2d, in a
+ * global-memory work matrix per CTA in 3d); levels set later use it.  With
+ * large patches the V-cycle runs the KERNELS engine (other engines are
+ * refused) and multi-vector calls are refused; call this before
+ * nmg_solve_many and before serving the hierarchy.  NMG_ERR_INVALID for a
+ * NULL hierarchy or after multi-vector solves; NMG_ERR_SINGULAR_PATCH if a
+ * refactored patch has a zero pivot. */
+nmg_status nmg_set_large_patches(nmg_hierarchy* h, const uint8_t* cell_mask);
+
+/* The patch layout of level (1..levels-1): *nsmall patches of *np_small
+ * unknowns (blocks of 2^dim cells) and *nlarge patches of *np_large unknowns
+ * (blocks of 4^dim cells; 0 without nmg_set_large_patches or where no large
+ * block fits).  nmg_get_patch_inverses numbers the small patches first (in
+ * origin order, x fastest), then the large ones (same order); a range must
+ * hold patches of one size.  Any output pointer may be NULL. */
+nmg_status nmg_patch_layout(nmg_hierarchy* h, int level, int64_t* nsmall, int64_t* nlarge, int* np_small,
+                            int* np_large);
+
 /* Copies count patch inverses of a level, starting at patch first, to host
  * memory out (count * n_p * n_p doubles, row-major A_i^{-1}, converted from the
- * precision's storage type).  Patches are ordered by origin with x fastest;
- * patch-local unknowns node-major over the 3^dim nodes (x fastest), then
- * component. */
+ * precision's storage type).  Patches are ordered by origin with x fastest
+ * (with large patches: see nmg_patch_layout); patch-local unknowns node-major
+ * over the 3^dim (large: 5^dim) nodes (x fastest), then component. */
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int precision, int64_t first,
                                   int64_t count, double* out);
 

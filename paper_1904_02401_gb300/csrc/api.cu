@@ -125,8 +125,12 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
     if (prof) {
         const double sv = (double)sizeof(T);
         const double si = prec == NMG_PREC_FP64 ? 8.0 : prec == NMG_PREC_FP32 ? 4.0 : 2.0;
-        h->prof_bytes = (double)g.patches * g.np * g.np * si + (double)g.nodes * g.nc * sv +
-                        (double)g.patches * g.np * sv;
+        const Mixed& M = L.mixed;
+        const double ps = M.on ? (double)M.nsmall : (double)g.patches;
+        const double pl = M.on ? (double)M.nlarge : 0.0;
+        const double npl = M.on ? (double)M.np_large : 0.0;
+        h->prof_bytes = (ps * g.np * g.np + pl * npl * npl) * si + (double)g.nodes * g.nc * sv +
+                        (ps * g.np + pl * npl) * sv;
     }
     // mode 3: the residual products of the finest level; algorithmic bytes = the
     // Q1 blocks of the matrix once, x, b and r once
@@ -153,18 +157,38 @@ static void smooth_level(Hierarchy* h, int l, int prec, const T* b, T* x, int st
         }
         const bool rec = prof && h->prof_used < (int)h->prof_ev.size() / 2;
         if (rec) cudaEventRecord(h->prof_ev[2 * h->prof_used], s);
-        if (prec == NMG_PREC_FP64)
-            launch_vanka_apply<double, double>(g, (const double*)P.inv, P.inv_stride, (const double*)d, (double*)P.corr, s);
-        else if (prec == NMG_PREC_FP32)
-            launch_vanka_apply<float, float>(g, (const float*)P.inv, P.inv_stride, (const float*)d, (float*)P.corr, s);
-        else
+        const Mixed& M = L.mixed;
+        const int64_t ns = M.on ? M.nsmall : -1;   // small patches: all of the level, or the listed ones
+        const int32_t* ids = M.on ? M.small_id : nullptr;
+        if (prec == NMG_PREC_FP64) {
+            launch_vanka_apply<double, double>(g, (const double*)P.inv, P.inv_stride, (const double*)d, (double*)P.corr, s,
+                                               ns, ids);
+            if (M.on)
+                launch_vanka_apply_large<double, double>(g, (const double*)M.inv_large[0], M.stride_large[0], M.large_org,
+                                                         M.nlarge, (const double*)d, (double*)M.corr_large[0], s);
+        } else if (prec == NMG_PREC_FP32) {
+            launch_vanka_apply<float, float>(g, (const float*)P.inv, P.inv_stride, (const float*)d, (float*)P.corr, s,
+                                             ns, ids);
+            if (M.on)
+                launch_vanka_apply_large<float, float>(g, (const float*)M.inv_large[1], M.stride_large[1], M.large_org,
+                                                       M.nlarge, (const float*)d, (float*)M.corr_large[1], s);
+        } else {
             launch_vanka_apply<float, __nv_bfloat16>(g, (const __nv_bfloat16*)P.inv, P.inv_stride, (const float*)d,
-                                                    (float*)P.corr, s);
+                                                    (float*)P.corr, s, ns, ids);
+            if (M.on)
+                launch_vanka_apply_large<float, __nv_bfloat16>(g, (const __nv_bfloat16*)M.inv_large[2], M.stride_large[2],
+                                                               M.large_org, M.nlarge, (const float*)d,
+                                                               (float*)M.corr_large[1], s);
+        }
         if (rec) {
             cudaEventRecord(h->prof_ev[2 * h->prof_used + 1], s);
             h->prof_used++;
         }
-        launch_vanka_update<T>(g, (const T*)P.corr, x, st == 0 && x_zero, omega, average, s);
+        if (M.on)
+            launch_vanka_update_mixed<T>(g, (const T*)P.corr, (const T*)M.corr_large[prec == NMG_PREC_FP64 ? 0 : 1],
+                                         M.nsmall * g.np, M.inc, M.inc_n, x, x, st == 0 && x_zero, omega, average, s);
+        else
+            launch_vanka_update<T>(g, (const T*)P.corr, x, st == 0 && x_zero, omega, average, s);
     }
 }
 
@@ -476,8 +500,11 @@ static double vcycle_bytes(const Hierarchy* h, int prec, int nu1, int nu2) {
         const Geom& g = h->lev[l].g;
         const double n = (double)g.nodes * g.nc;
         const double mat = (double)g.nst * g.nc * g.nc * g.nodes * sv;
-        const double inv = (double)g.patches * g.np * g.np * si;
-        const double corr = (double)g.patches * g.np * sv;
+        const Mixed& M = h->lev[l].mixed;
+        const double ps = M.on ? (double)M.nsmall : (double)g.patches, pl = M.on ? (double)M.nlarge : 0.0;
+        const double npl = M.on ? (double)M.np_large : 0.0;
+        const double inv = (ps * g.np * g.np + pl * npl * npl) * si;
+        const double corr = (ps * g.np + pl * npl) * sv;
         const int steps = nu1 + nu2;
         const int residuals = (nu1 > 0 ? nu1 - 1 : 0) + 1 + nu2;
         bytes += steps * (inv + 2.0 * corr + 3.0 * n) + residuals * (mat + 3.0 * n);
@@ -509,9 +536,10 @@ static nmg_status run_engine(Hierarchy* h, const nmg_solve_opts& o, int engine) 
 // The fastest is kept per precision and (nu1, nu2, weighting).
 static nmg_status resolve_engine(Hierarchy* h, const nmg_solve_opts& o, int* engine) {
     const int prec = o.precision;
-    if (h->nc == h->dim) {   // n_c = d (vector problems): per-step kernels only, no cluster tail, no tiles
+    if (h->nc == h->dim || h->mixed_any) {   // vector problems or patches of two sizes: per-step kernels only
         if (o.engine != NMG_ENGINE_AUTO && o.engine != NMG_ENGINE_KERNELS)
-            return fail(NMG_ERR_INVALID, "hierarchies with ncomp = dim run the KERNELS engine only");
+            return fail(NMG_ERR_INVALID,
+                        "hierarchies with ncomp = dim or with patches of two sizes run the KERNELS engine only");
         h->tail_patches[prec] = 0;
         h->tile_patches[prec] = 0;
         h->fused[prec] = 0;
@@ -817,6 +845,7 @@ static nmg_status check_many(Hierarchy* h, const nmg_solve_opts& o) {
     if (o.precision != NMG_PREC_FP32 && o.precision != NMG_PREC_BF16)
         return fail(NMG_ERR_INVALID, "multi-vector V-cycles run in precision FP32 or BF16");
     if (!many_layout_ok(h, o.precision)) return fail(NMG_ERR_INVALID, "patch inverse layout");
+    if (h->mixed_any) return fail(NMG_ERR_INVALID, "multi-vector V-cycles need patches of one size");
     return NMG_OK;
 }
 
@@ -1327,6 +1356,8 @@ static nmg_status alloc_workspace(Hierarchy* h) {
 // solves), so that two requests on one hierarchy run at the same time with the
 // same kernels on the same data (bitwise the same results).  budget: bytes the
 // workspace may take (0 = unlimited).  The autotuner's choices are copied.
+static nmg_status mixed_alloc(Hierarchy* h, Mixed& M, void** p, size_t bytes);
+
 static nmg_status clone_workspace(Hierarchy* base, size_t budget, Hierarchy** out) {
     *out = nullptr;
     auto* h = new nmg_hierarchy();
@@ -1351,7 +1382,23 @@ static nmg_status clone_workspace(Hierarchy* base, size_t budget, Hierarchy** ou
             Lv.p[p].inv = B.p[p].inv;
             Lv.p[p].inv_stride = B.p[p].inv_stride;
         }
+        if (B.mixed.on) {   // the layout and large inverses are shared; the corrections are the clone's own
+            Mixed& M = Lv.mixed;
+            M.on = true;
+            M.nsmall = B.mixed.nsmall;
+            M.nlarge = B.mixed.nlarge;
+            M.np_large = B.mixed.np_large;
+            M.small_id = B.mixed.small_id;
+            M.large_org = B.mixed.large_org;
+            M.inc = B.mixed.inc;
+            M.inc_n = B.mixed.inc_n;
+            for (int p = 0; p < 3; ++p) {
+                M.inv_large[p] = B.mixed.inv_large[p];
+                M.stride_large[p] = B.mixed.stride_large[p];
+            }
+        }
     }
+    h->mixed_any = base->mixed_any;
     for (int p = 0; p < 3; ++p) {
         h->engine_choice[p] = base->engine_choice[p];
         h->auto_tail[p] = base->auto_tail[p];
@@ -1366,6 +1413,13 @@ static nmg_status clone_workspace(Hierarchy* base, size_t budget, Hierarchy** ou
     if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
         st = fail(NMG_ERR_CUDA, "stream creation failed");
     if (st == NMG_OK) st = alloc_workspace(h);
+    for (int l = 1; l < h->L && st == NMG_OK; ++l) {
+        Mixed& M = h->lev[l].mixed;
+        if (!M.on) continue;
+        const size_t n = (size_t)M.nlarge * M.np_large;
+        if (h->prec_mask & 1) st = mixed_alloc(h, M, &M.corr_large[0], n * sizeof(double));
+        if (st == NMG_OK && (h->prec_mask & 6)) st = mixed_alloc(h, M, &M.corr_large[1], n * sizeof(float));
+    }
     if (st != NMG_OK) {
         free_all(h);
         delete h;
@@ -1622,6 +1676,140 @@ static nmg_status load_stencil(Hierarchy* h, const Geom& g, int64_t nrows_blk, i
     return st;
 }
 
+// ---- patches of two sizes (Section 5.5.1)
+
+static void dfree(Hierarchy* h, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+        if (*it == p) {
+            h->allocs.erase(it);
+            break;
+        }
+    h->bytes -= bytes;
+}
+
+static nmg_status mixed_alloc(Hierarchy* h, Mixed& M, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    NMG_TRY(dalloc(h, p, bytes));
+    M.owned.emplace_back(*p, bytes);
+    return NMG_OK;
+}
+
+static void release_mixed(Hierarchy* h, Mixed& M) {
+    for (auto& a : M.owned) dfree(h, a.first, a.second);
+    M = Mixed();
+}
+
+// The patch layout of level l for the flagged cells cmask (x fastest): large
+// patches on the 4-aligned blocks of 4^d cells that are all flagged, small
+// patches on the other 2-aligned blocks of 2^d cells, and the per-node
+// incidence of both.  No large block: the level keeps its single patch size.
+static nmg_status build_mixed(Hierarchy* h, int l, const std::vector<uint8_t>& cmask) {
+    Level& Lv = h->lev[l];
+    const Geom& g = Lv.g;
+    Mixed& M = Lv.mixed;
+    const int d = g.dim;
+    const int64_t c0 = g.cells[0], c1 = g.cells[1];
+    std::vector<uint8_t> covered(g.patches, 0);
+    std::vector<int32_t> large, small;
+    const int zb = d == 3 ? g.cells[2] : 1;
+    for (int bz = 0; d == 2 ? bz == 0 : bz + 4 <= zb; bz += 4)
+        for (int by = 0; by + 4 <= g.cells[1]; by += 4)
+            for (int bx = 0; bx + 4 <= g.cells[0]; bx += 4) {
+                bool all = true;
+                for (int z = bz; z < (d == 3 ? bz + 4 : 1) && all; ++z)
+                    for (int y = by; y < by + 4 && all; ++y)
+                        for (int x = bx; x < bx + 4 && all; ++x) all = cmask[x + c0 * (y + c1 * z)] != 0;
+                if (!all) continue;
+                const int64_t px = bx / 2, py = by / 2, pz = bz / 2;
+                large.push_back((int32_t)(px + g.pc[0] * (py + (int64_t)g.pc[1] * pz)));
+                for (int k = 0; k < (d == 3 ? 2 : 1); ++k)
+                    for (int j = 0; j < 2; ++j)
+                        for (int i = 0; i < 2; ++i)
+                            covered[(px + i) + g.pc[0] * ((py + j) + (int64_t)g.pc[1] * (pz + k))] = 1;
+            }
+    if (large.empty()) return NMG_OK;
+    for (int64_t q = 0; q < g.patches; ++q)
+        if (!covered[q]) small.push_back((int32_t)q);
+    const int nc = g.nc, nps = g.np;
+    const int npl = (d == 2 ? 25 : 125) * nc;
+    if ((double)small.size() * nps + (double)large.size() * npl >= 2147483647.0)
+        return fail(NMG_ERR_INVALID, "too many patch unknowns on a level for the incidence table");
+    std::vector<int32_t> inc((size_t)g.nodes * kIncMax, -1);
+    std::vector<uint8_t> inc_n(g.nodes, 0);
+    auto add = [&](int64_t node, int64_t off) -> bool {
+        uint8_t& n = inc_n[node];
+        if (n >= kIncMax) return false;
+        inc[node * kIncMax + n++] = (int32_t)off;
+        return true;
+    };
+    const int64_t n0 = g.nn[0], n1 = g.nn[1];
+    bool ok = true;
+    for (size_t k = 0; k < small.size() && ok; ++k) {
+        const int64_t q = small[k];
+        const int64_t px = q % g.pc[0], py = (q / g.pc[0]) % g.pc[1], pz = q / ((int64_t)g.pc[0] * g.pc[1]);
+        for (int an = 0; an < (d == 2 ? 9 : 27) && ok; ++an) {
+            const int ax = an % 3, ay = (an / 3) % 3, az = an / 9;
+            ok = add((2 * px + ax) + n0 * ((2 * py + ay) + n1 * (2 * pz + az)), (int64_t)k * nps + (int64_t)an * nc);
+        }
+    }
+    const int64_t base = (int64_t)small.size() * nps;
+    for (size_t m = 0; m < large.size() && ok; ++m) {
+        const int64_t q = large[m];
+        const int64_t px = q % g.pc[0], py = (q / g.pc[0]) % g.pc[1], pz = q / ((int64_t)g.pc[0] * g.pc[1]);
+        for (int an = 0; an < (d == 2 ? 25 : 125) && ok; ++an) {
+            const int ax = an % 5, ay = (an / 5) % 5, az = an / 25;
+            ok = add((2 * px + ax) + n0 * ((2 * py + ay) + n1 * (2 * pz + az)),
+                     base + (int64_t)m * npl + (int64_t)an * nc);
+        }
+    }
+    if (!ok) return fail(NMG_ERR_INVALID, "a node lies in more patches than the incidence table holds");
+    M.nsmall = (int64_t)small.size();
+    M.nlarge = (int64_t)large.size();
+    M.np_large = npl;
+    NMG_TRY(mixed_alloc(h, M, (void**)&M.small_id, small.size() * sizeof(int32_t)));
+    NMG_TRY(mixed_alloc(h, M, (void**)&M.large_org, large.size() * sizeof(int32_t)));
+    NMG_TRY(mixed_alloc(h, M, (void**)&M.inc, inc.size() * sizeof(int32_t)));
+    NMG_TRY(mixed_alloc(h, M, (void**)&M.inc_n, inc_n.size()));
+    NMG_CK(cudaMemcpy(M.small_id, small.data(), small.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    NMG_CK(cudaMemcpy(M.large_org, large.data(), large.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    NMG_CK(cudaMemcpy(M.inc, inc.data(), inc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    NMG_CK(cudaMemcpy(M.inc_n, inc_n.data(), inc_n.size(), cudaMemcpyHostToDevice));
+    for (int p = 0; p < 3; ++p) {
+        if (!(h->prec_mask & (1 << p))) continue;
+        M.stride_large[p] = pad16((int64_t)npl * npl, store_size(p));
+        NMG_TRY(mixed_alloc(h, M, &M.inv_large[p], (size_t)M.nlarge * M.stride_large[p] * store_size(p)));
+    }
+    if (h->prec_mask & 1) NMG_TRY(mixed_alloc(h, M, &M.corr_large[0], (size_t)M.nlarge * npl * sizeof(double)));
+    if (h->prec_mask & 6) NMG_TRY(mixed_alloc(h, M, &M.corr_large[1], (size_t)M.nlarge * npl * sizeof(float)));
+    M.on = true;
+    return NMG_OK;
+}
+
+// Extracts and inverts every patch matrix of level l >= 1 from its FP64
+// stencil matrix, in the level's patch layout (one size, or two sizes with
+// the small patches listed), storing the inverses in every prepared precision.
+static nmg_status factor_patches(Hierarchy* h, int l) {
+    Level& Lv = h->lev[l];
+    const Geom& g = Lv.g;
+    cudaStream_t s = h->stream;
+    PrecData* P = Lv.p;
+    const bool p64 = h->prec_mask & 1, p32 = h->prec_mask & 2, pbf = h->prec_mask & 4;
+    const Mixed& M = Lv.mixed;
+    NMG_CK(launch_patch_invert(g, Lv.A64, p64 ? (double*)P[0].inv : nullptr, P[0].inv_stride,
+                               p32 ? (float*)P[1].inv : nullptr, P[1].inv_stride,
+                               pbf ? (__nv_bfloat16*)P[2].inv : nullptr, P[2].inv_stride, h->flags, s,
+                               M.on ? M.nsmall : -1, M.on ? M.small_id : nullptr));
+    if (M.on)
+        NMG_CK(launch_patch_invert_large(g, Lv.A64, M.large_org, M.nlarge,
+                                         p64 ? (double*)M.inv_large[0] : nullptr, M.stride_large[0],
+                                         p32 ? (float*)M.inv_large[1] : nullptr, M.stride_large[1],
+                                         pbf ? (__nv_bfloat16*)M.inv_large[2] : nullptr, M.stride_large[2],
+                                         h->flags, s));
+    return NMG_OK;
+}
+
 extern "C" {
 
 nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
@@ -1639,11 +1827,7 @@ nmg_status nmg_set_jacobian(nmg_hierarchy* h, int level, int64_t nrows_blk, int6
         launch_convert_f64_f32(Lv.A64, (float*)A32, (int64_t)mat, s);
     }
     if (level > 0) {
-        PrecData* P = Lv.p;
-        const bool p64 = h->prec_mask & 1, p32 = h->prec_mask & 2, pbf = h->prec_mask & 4;
-        NMG_CK(launch_patch_invert(g, Lv.A64, p64 ? (double*)P[0].inv : nullptr, P[0].inv_stride,
-                                   p32 ? (float*)P[1].inv : nullptr, P[1].inv_stride,
-                                   pbf ? (__nv_bfloat16*)P[2].inv : nullptr, P[2].inv_stride, h->flags, s));
+        NMG_TRY(factor_patches(h, level));
     } else {
         const int64_t n0 = h->n0;
         int* perm = nullptr;
@@ -1824,20 +2008,28 @@ nmg_status nmg_solve_many(nmg_hierarchy* h, int nrhs, const double* b, double* x
 nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int prec, int64_t first, int64_t count, double* out) {
     NMG_TRY(op_check(h, level, prec, true));
     const Geom& g = h->lev[level].g;
-    if (first < 0 || count < 0 || first + count > g.patches || (count && !out))
+    const Mixed& M = h->lev[level].mixed;
+    const int64_t ns = M.on ? M.nsmall : g.patches, total = M.on ? M.nsmall + M.nlarge : g.patches;
+    if (first < 0 || count < 0 || first + count > total || (count && !out))
         return fail(NMG_ERR_INVALID, "patch range out of bounds");
+    const bool large = M.on && first >= ns;
+    if (count && M.on && first < ns && first + count > ns)
+        return fail(NMG_ERR_INVALID, "a patch range holds patches of one size only");
     enter(h);
     const PrecData& P = h->lev[level].p[prec];
+    const void* base = large ? M.inv_large[prec] : P.inv;
+    const int64_t stride = large ? M.stride_large[prec] : P.inv_stride;
+    const int64_t k0 = large ? first - ns : first;
     const size_t es = store_size(prec);
-    std::vector<unsigned char> buf((size_t)count * P.inv_stride * es);
-    NMG_CK(cudaMemcpyAsync(buf.data(), (const unsigned char*)P.inv + (size_t)first * P.inv_stride * es, buf.size(),
+    std::vector<unsigned char> buf((size_t)count * stride * es);
+    NMG_CK(cudaMemcpyAsync(buf.data(), (const unsigned char*)base + (size_t)k0 * stride * es, buf.size(),
                            cudaMemcpyDeviceToHost, h->stream));
     NMG_CK(cudaStreamSynchronize(h->stream));
-    const int np = g.np;
+    const int np = large ? M.np_large : g.np;
     for (int64_t p = 0; p < count; ++p)
         for (int j = 0; j < np; ++j)
             for (int i = 0; i < np; ++i) {
-                const size_t idx = (size_t)p * P.inv_stride + (size_t)j * np + i;
+                const size_t idx = (size_t)p * stride + (size_t)j * np + i;
                 double v;
                 if (prec == NMG_PREC_FP64) v = ((const double*)buf.data())[idx];
                 else if (prec == NMG_PREC_FP32) v = ((const float*)buf.data())[idx];
@@ -1847,7 +2039,72 @@ nmg_status nmg_get_patch_inverses(nmg_hierarchy* h, int level, int prec, int64_t
     return NMG_OK;
 }
 
+nmg_status nmg_patch_layout(nmg_hierarchy* h, int level, int64_t* nsmall, int64_t* nlarge, int* np_small,
+                            int* np_large) {
+    if (!h) return fail(NMG_ERR_INVALID, "NULL hierarchy");
+    if (level < 1 || level >= h->L) return fail(NMG_ERR_INVALID, "level out of range (the coarsest has no patches)");
+    const Geom& g = h->lev[level].g;
+    const Mixed& M = h->lev[level].mixed;
+    if (nsmall) *nsmall = M.on ? M.nsmall : g.patches;
+    if (nlarge) *nlarge = M.on ? M.nlarge : 0;
+    if (np_small) *np_small = g.np;
+    if (np_large) *np_large = (g.dim == 2 ? 25 : 125) * g.nc;
+    return NMG_OK;
+}
+
 // ---- problems (2) and (3) of Section 4.2 around the momentum solve
+
+nmg_status nmg_set_large_patches(nmg_hierarchy* h, const uint8_t* cell_mask) {
+    if (!h) return fail(NMG_ERR_INVALID, "NULL hierarchy");
+    if (!h->many_ws.empty()) return fail(NMG_ERR_INVALID, "set the patch layout before multi-vector solves");
+    enter(h);
+    NMG_CK(cudaStreamSynchronize(h->stream));
+    for (int l = 1; l < h->L; ++l) release_mixed(h, h->lev[l].mixed);
+    h->mixed_any = false;
+    nmg_status st = NMG_OK;
+    if (cell_mask) {
+        const Geom& gf = h->lev[h->L - 1].g;
+        auto cz = [&](const Geom& q) { return (size_t)(h->dim == 3 ? q.cells[2] : 1); };   // cells[2] is 0 in 2d
+        std::vector<uint8_t> m(cell_mask, cell_mask + (size_t)gf.cells[0] * gf.cells[1] * cz(gf));
+        for (int l = h->L - 1; l >= 1 && st == NMG_OK; --l) {
+            st = build_mixed(h, l, m);
+            h->mixed_any = h->mixed_any || h->lev[l].mixed.on;
+            // the next coarser level: a cell is flagged iff all its children are
+            const Geom& g = h->lev[l].g;
+            const Geom& c = h->lev[l - 1].g;
+            std::vector<uint8_t> cm((size_t)c.cells[0] * c.cells[1] * cz(c));
+            for (int z = 0; z < (int)cz(c); ++z)
+                for (int y = 0; y < c.cells[1]; ++y)
+                    for (int x = 0; x < c.cells[0]; ++x) {
+                        bool all = true;
+                        for (int k = 0; k < (h->dim == 3 ? 2 : 1); ++k)
+                            for (int j = 0; j < 2; ++j)
+                                for (int i = 0; i < 2; ++i)
+                                    all = all && m[(2 * x + i) + (size_t)g.cells[0] * ((2 * y + j) +
+                                                                   (size_t)g.cells[1] * (2 * z + k))];
+                        cm[x + (size_t)c.cells[0] * (y + (size_t)c.cells[1] * z)] = all;
+                    }
+            m.swap(cm);
+        }
+    }
+    if (st != NMG_OK) {
+        for (int l = 1; l < h->L; ++l) release_mixed(h, h->lev[l].mixed);
+        h->mixed_any = false;
+    }
+    // graphs and engine choices were made for the old layout
+    for (int p = 0; p < 3; ++p) {
+        if (h->vgraph[p]) { cudaGraphExecDestroy(h->vgraph[p]); h->vgraph[p] = nullptr; }
+        if (h->cgraph[p]) { cudaGraphExecDestroy(h->cgraph[p]); h->cgraph[p] = nullptr; }
+        h->engine_choice[p] = 0;
+    }
+    // refactor the levels already set, in the new layout
+    for (int l = 1; l < h->L && st == NMG_OK; ++l)
+        if (h->lev[l].ready) {
+            st = factor_patches(h, l);
+            if (st == NMG_OK) st = check_flags(h);
+        }
+    return st;
+}
 
 nmg_status nmg_set_lifting_operator(nmg_hierarchy* h, int64_t nrows_blk, int64_t nnzb, const int64_t* row_ptr,
                                     const int32_t* col_idx, const double* vals, int ptr_location) {
@@ -2291,7 +2548,7 @@ static void server_loop(Server* S) {
                 auto fits_with = [&](size_t need) { return S->budget == 0 || used + need <= S->budget || first; };
                 Hierarchy* slot = nullptr;
                 Group* G = S->groups.count(r->h) ? S->groups[r->h] : nullptr;
-                const bool batch = S->batch_columns > 1 && r->o.precision != NMG_PREC_FP64;
+                const bool batch = S->batch_columns > 1 && r->o.precision != NMG_PREC_FP64 && !r->h->mixed_any;
                 if (batch) {
                     // a column of the hierarchy's group (none runs alone on it)
                     int k = -1;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/nmg.h"
@@ -63,9 +64,34 @@ struct MultiData {
     float* corr = nullptr;        // patches * n_p * K
 };
 
+// Patches of two sizes on a level (Section 5.5.1; nmg_set_large_patches).
+// nsmall blocks of 2^d cells, listed by their index on the level's regular
+// patch grid (small_id), with their inverses and corrections stored in list
+// order in the level's regular buffers; nlarge blocks of 4^d cells (5^d
+// nodes, np_large unknowns), listed by the regular index of their lowest
+// 2^d-cell block (large_org), with inverses and corrections of their own.
+// inc: per node kIncMax offsets of its correction entries (component 0) in
+// the concatenation [small corrections, large corrections], in patch order;
+// inc_n: how many.
+constexpr int kIncMax = 8;
+struct Mixed {
+    bool on = false;
+    int64_t nsmall = 0, nlarge = 0;
+    int np_large = 0;
+    int32_t* small_id = nullptr;
+    int32_t* large_org = nullptr;
+    int32_t* inc = nullptr;
+    uint8_t* inc_n = nullptr;
+    void* inv_large[3] = {nullptr, nullptr, nullptr};
+    int64_t stride_large[3] = {0, 0, 0};
+    void* corr_large[2] = {nullptr, nullptr};    // FP64 / FP32 (shared by FP32 and BF16)
+    std::vector<std::pair<void*, size_t>> owned;  // allocations to release when the layout changes
+};
+
 struct Level {
     Geom g;
     bool ready = false;
+    Mixed mixed;
     double* A64 = nullptr;        // FP64 stencil matrix (always kept: outer FGMRES + FP64 mode)
     uint8_t* mask = nullptr;      // Dirichlet flag per unknown
     PrecData p[3];                // NMG_PREC_FP64 / FP32 / BF16
@@ -121,6 +147,7 @@ struct Hierarchy {
     // persistent V-cycle: grid barrier state and the engine AUTO picked per precision
     unsigned* pbar = nullptr;
     int wait_limit = 0;                  // > 0: iteration limit of the persistent grid-barrier wait
+    bool mixed_any = false;              // some level has patches of two sizes
     // extension problems (ncomp = dim): the finest level's operator before the reduction of its
     // fixed rows and columns (stencil layout, FP64), and the work vectors of nmg_newton_substeps
     double* lift64 = nullptr;
@@ -179,7 +206,11 @@ void launch_bsr_to_stencil(const Geom& g, const int64_t* row_ptr, const int32_t*
 void launch_convert_f64_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 cudaError_t launch_patch_invert(const Geom& g, const double* A64, double* inv64, int64_t s64,
                                 float* inv32, int64_t s32, __nv_bfloat16* invbf, int64_t sbf,
-                                int* flags, cudaStream_t s);
+                                int* flags, cudaStream_t s, int64_t npatch = -1, const int32_t* ids = nullptr);
+// Large patches (4^d cells) listed by org (their lowest 2^d-cell block on the regular patch grid).
+cudaError_t launch_patch_invert_large(const Geom& g, const double* A64, const int32_t* org, int64_t npatch,
+                                      double* inv64, int64_t s64, float* inv32, int64_t s32, __nv_bfloat16* invbf,
+                                      int64_t sbf, int* flags, cudaStream_t s);
 void launch_coarse_assemble(const Geom& g, const double* A64, double* dense, cudaStream_t s);
 void launch_dense_invert(double* a, int64_t n, int* perm, int* flags, cudaStream_t s);
 
@@ -189,9 +220,11 @@ void launch_dense_invert(double* a, int64_t n, int* perm, int* flags, cudaStream
 template <typename T>
 void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual,
                  cudaStream_t s);
+// npatch >= 0 with ids: the listed patches only (ids[k] = the patch's index on
+// the level's regular patch grid; inverse k and correction k stored in list order).
 template <typename T, typename TS>
 void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr,
-                        cudaStream_t s);
+                        cudaStream_t s, int64_t npatch = -1, const int32_t* ids = nullptr);
 template <typename T>
 void launch_vanka_update(const Geom& g, const T* corr, T* x, bool x_zero, T omega, bool average,
                          cudaStream_t s);
@@ -314,6 +347,17 @@ extern thread_local int64_t g_launches;
 // ---------------------------------------------------------------------------
 // Launchers (coupling.cu): problems (2) and (3) of Section 4.2, FP64
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Launchers (mixed_kernels.cu): patches of two sizes
+// ---------------------------------------------------------------------------
+template <typename T, typename TS>
+void launch_vanka_apply_large(const Geom& g, const TS* inv, int64_t stride, const int32_t* org, int64_t npatch,
+                              const T* d, T* corr, cudaStream_t s);
+template <typename T>
+void launch_vanka_update_mixed(const Geom& g, const T* corr_s, const T* corr_l, int64_t nsm, const int32_t* inc,
+                               const uint8_t* inc_n, const T* x_in, T* x_out, bool x_zero, T omega, bool average,
+                               cudaStream_t s);
+
 void launch_deformation_update(int dim, int64_t nodes, const double* r, const double* dv, double k_theta,
                                const uint8_t* update_nodes, double* du, cudaStream_t s);
 void launch_extension_rhs(const Geom& g, const double* E, const uint8_t* fixed, const double* b5, const double* gv,

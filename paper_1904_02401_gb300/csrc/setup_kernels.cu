@@ -1,6 +1,8 @@
 // Set-up kernels: matrix layout conversion, Vanka patch extraction and exact
 // inversion (Section 4.3: A_i = R_i A R_i^T, "inverted exactly"), coarse
 // matrix inversion.  All set-up arithmetic is FP64.
+#include <algorithm>
+
 #include "nmg_internal.cuh"
 
 namespace nmg {
@@ -130,7 +132,8 @@ __device__ void gauss_jordan_smem(double* a, double* col, int* perm, int* s_piv,
 template <int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256)
 k_patch_invert(Geom g, const double* __restrict__ A, double* inv64, int64_t s64, float* inv32,
-               int64_t s32, __nv_bfloat16* invbf, int64_t sbf, int* flags) {
+               int64_t s32, __nv_bfloat16* invbf, int64_t sbf, int* flags, int64_t npatch,
+               const int32_t* __restrict__ ids) {
     constexpr int NN = (DIM == 2) ? 9 : 27;      // nodes per patch
     constexpr int NP = NN * NC;
     constexpr int LDA = NP + 1;
@@ -142,10 +145,11 @@ k_patch_invert(Geom g, const double* __restrict__ A, double* inv64, int64_t s64,
     __shared__ double s_pval;
     __shared__ bool s_sing;
     const int tid = threadIdx.x;
-    for (int64_t p = blockIdx.x; p < g.patches; p += gridDim.x) {
-        const int px = (int)(p % g.pc[0]);
-        const int py = (int)((p / g.pc[0]) % g.pc[1]);
-        const int pz = (int)(p / ((int64_t)g.pc[0] * g.pc[1]));
+    for (int64_t p = blockIdx.x; p < npatch; p += gridDim.x) {
+        const int64_t q = ids ? (int64_t)ids[p] : p;     // index on the regular patch grid
+        const int px = (int)(q % g.pc[0]);
+        const int py = (int)((q / g.pc[0]) % g.pc[1]);
+        const int pz = (int)(q / ((int64_t)g.pc[0] * g.pc[1]));
         if (tid == 0) s_sing = false;
         for (int idx = tid; idx < NP * NP; idx += blockDim.x) {
             const int row = idx / NP, cl = idx - row * NP;
@@ -169,6 +173,66 @@ k_patch_invert(Geom g, const double* __restrict__ A, double* inv64, int64_t s64,
         for (int idx = tid; idx < NP * NP; idx += blockDim.x) {
             const int j = idx / NP, i = idx - j * NP;          // column-major output
             const double v = a[i * LDA + j];
+            if (inv64) inv64[p * s64 + idx] = v;
+            if (inv32) inv32[p * s32 + idx] = (float)v;
+            if (invbf) invbf[p * sbf + idx] = __double2bfloat16(v);
+        }
+        __syncthreads();
+    }
+}
+
+// Large patches (blocks of 4^d cells, 5^d nodes): A_P gathered from the
+// stencil matrix (nodes more than one apart in a direction do not couple),
+// inverted by the Gauss-Jordan elimination with partial pivoting above and
+// stored column-major in every requested precision.  2d (75 or 50 unknowns):
+// the matrix in shared memory; 3d (500 or 375 unknowns, 2 MB in FP64): in a
+// global work matrix of the CTA (L2-resident), the pivot column and
+// permutation in shared memory.  org[p]: the patch's lowest 2^d-cell block on
+// the regular patch grid.
+template <int DIM, int NC, bool SMEM>
+__global__ void __launch_bounds__(SMEM ? 256 : 1024)
+k_patch_invert_large(Geom g, const double* __restrict__ A, const int32_t* __restrict__ org, int64_t npatch,
+                     double* work, double* inv64, int64_t s64, float* inv32, int64_t s32, __nv_bfloat16* invbf,
+                     int64_t sbf, int* flags) {
+    constexpr int NN = (DIM == 2) ? 25 : 125;
+    constexpr int NP = NN * NC;
+    constexpr int LDA = SMEM ? NP + 1 : NP;
+    extern __shared__ double smem[];
+    double* a = SMEM ? smem : work + (int64_t)blockIdx.x * NP * LDA;
+    double* col = SMEM ? smem + NP * LDA : smem;
+    int* perm = reinterpret_cast<int*>(col + NP);
+    __shared__ int s_piv;
+    __shared__ double s_pval;
+    __shared__ bool s_sing;
+    const int tid = threadIdx.x;
+    for (int64_t p = blockIdx.x; p < npatch; p += gridDim.x) {
+        const int64_t q = org[p];
+        const int px = (int)(q % g.pc[0]);
+        const int py = (int)((q / g.pc[0]) % g.pc[1]);
+        const int pz = (int)(q / ((int64_t)g.pc[0] * g.pc[1]));
+        if (tid == 0) s_sing = false;
+        for (int idx = tid; idx < NP * NP; idx += blockDim.x) {
+            const int row = idx / NP, cl = idx - row * NP;
+            const int an = row / NC, r = row - an * NC;
+            const int bn = cl / NC, c = cl - bn * NC;
+            const int ax = an % 5, ay = (an / 5) % 5, az = an / 25;
+            const int bx = bn % 5, by = (bn / 5) % 5, bz = bn / 25;
+            const int dx = bx - ax, dy = by - ay, dz = bz - az;
+            double v = 0.0;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) {
+                const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+                const int64_t node = (int64_t)(2 * px + ax) +
+                                     (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
+                v = A[((int64_t)s * NC * NC + r * NC + c) * g.ld + node];
+            }
+            a[(int64_t)row * LDA + cl] = v;
+        }
+        __syncthreads();
+        gauss_jordan_smem<NP, LDA>(a, col, perm, &s_piv, &s_pval, &s_sing);
+        if (tid == 0 && s_sing) atomicOr(&flags[FLAG_SINGULAR], 1);
+        for (int idx = tid; idx < NP * NP; idx += blockDim.x) {
+            const int j = idx / NP, i = idx - j * NP;          // column-major output
+            const double v = a[(int64_t)i * LDA + j];
             if (inv64) inv64[p * s64 + idx] = v;
             if (inv32) inv32[p * s32 + idx] = (float)v;
             if (invbf) invbf[p * sbf + idx] = __double2bfloat16(v);
@@ -297,14 +361,15 @@ void launch_convert_f64_f32(const double* in, float* out, int64_t n, cudaStream_
 
 cudaError_t launch_patch_invert(const Geom& g, const double* A64, double* inv64, int64_t s64,
                                 float* inv32, int64_t s32, __nv_bfloat16* invbf, int64_t sbf,
-                                int* flags, cudaStream_t s) {
+                                int* flags, cudaStream_t s, int64_t npatch, const int32_t* ids) {
     g_launches += 1;
+    if (npatch < 0) npatch = g.patches;
     const int NN = g.dim == 2 ? 9 : 27;
     const int NP = NN * g.nc;
     const size_t smem = (size_t)NP * (NP + 1) * sizeof(double) + NP * sizeof(double) + NP * sizeof(int);
     const int per_sm = g.dim == 2 ? 8 : 2;
     int64_t grid = (int64_t)sm_count() * per_sm;
-    if (grid > g.patches) grid = g.patches;
+    if (grid > npatch) grid = npatch;
     if (grid < 1) return cudaSuccess;
     cudaError_t e;
     const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
@@ -312,8 +377,39 @@ cudaError_t launch_patch_invert(const Geom& g, const double* A64, double* inv64,
                            : (lean ? k_patch_invert<3, 3> : k_patch_invert<3, 4>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)grid, 256, smem, s>>>(g, A64, inv64, s64, inv32, s32, invbf, sbf, flags);
+    kern<<<(unsigned)grid, 256, smem, s>>>(g, A64, inv64, s64, inv32, s32, invbf, sbf, flags, npatch, ids);
     return cudaGetLastError();
+}
+
+cudaError_t launch_patch_invert_large(const Geom& g, const double* A64, const int32_t* org, int64_t npatch,
+                                      double* inv64, int64_t s64, float* inv32, int64_t s32, __nv_bfloat16* invbf,
+                                      int64_t sbf, int* flags, cudaStream_t s) {
+    if (npatch <= 0) return cudaSuccess;
+    g_launches += 1;
+    const bool lean = g.nc == g.dim;
+    const int NP = (g.dim == 2 ? 25 : 125) * g.nc;
+    cudaError_t e;
+    if (g.dim == 2) {
+        const size_t smem = (size_t)NP * (NP + 1) * sizeof(double) + NP * sizeof(double) + NP * sizeof(int);
+        auto kern = lean ? k_patch_invert_large<2, 2, true> : k_patch_invert_large<2, 3, true>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::min<int64_t>(npatch, (int64_t)sm_count() * 4);
+        kern<<<(unsigned)grid, 256, smem, s>>>(g, A64, org, npatch, nullptr, inv64, s64, inv32, s32, invbf, sbf, flags);
+        return cudaGetLastError();
+    }
+    // 3d: one work matrix per CTA in global memory (freed once the launch has completed)
+    const int64_t grid = std::min<int64_t>(npatch, (int64_t)sm_count());
+    double* work = nullptr;
+    e = cudaMalloc(&work, (size_t)grid * NP * NP * sizeof(double));
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)NP * sizeof(double) + NP * sizeof(int);
+    auto kern = lean ? k_patch_invert_large<3, 3, false> : k_patch_invert_large<3, 4, false>;
+    kern<<<(unsigned)grid, 1024, smem, s>>>(g, A64, org, npatch, work, inv64, s64, inv32, s32, invbf, sbf, flags);
+    e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(work);
+    return e != cudaSuccess ? e : e2;
 }
 
 void launch_coarse_assemble(const Geom& g, const double* A64, double* dense, cudaStream_t s) {

@@ -56,14 +56,14 @@ k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* _
 template <typename T, typename TS, int DIM, int WARPS, int NC = DIM + 1>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
-              T* __restrict__ corr) {
+              T* __restrict__ corr, int64_t npatch, const int32_t* __restrict__ ids) {
     NMG_PDL_ENTRY();
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     __shared__ T sd[WARPS][NP];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * WARPS + w;
-    if (p >= g.patches) return;
-    gather_patch<T, DIM, NC>(g, d, p, sd[w], lane);
+    if (p >= npatch) return;
+    gather_patch<T, DIM, NC>(g, d, ids ? (int64_t)ids[p] : p, sd[w], lane);
     __syncwarp();
     apply_patch<T, TS, DIM, true, NC>(inv + p * stride, sd[w], corr + p * NP, lane);
 }
@@ -81,7 +81,7 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 template <typename T, typename TS, int DIM, int STAGES, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
 k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
-                   T* __restrict__ corr) {
+                   T* __restrict__ corr, int64_t npatch, const int32_t* __restrict__ ids) {
     constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     constexpr int RW = NP / 27;                    // warps per patch
@@ -94,21 +94,21 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int q = w / RW, row = (w % RW) * 27 + lane;
     const int64_t G = gridDim.x;
-    const int64_t nchunks = (g.patches + CP - 1) / CP;
+    const int64_t nchunks = (npatch + CP - 1) / CP;
     const int64_t mine = (nchunks - blockIdx.x + G - 1) / G;   // the grid is at most nchunks
     const int64_t stage_elems = (int64_t)CP * stride;
     auto issue = [&](int64_t k) {
         const int64_t c = blockIdx.x + k * G;
-        const int cnt = (int)min((int64_t)CP, g.patches - c * CP);
+        const int cnt = (int)min((int64_t)CP, npatch - c * CP);
         bulk_copy(ring + (k % STAGES) * stage_elems, inv + c * CP * stride,
                   (uint32_t)(cnt * stride * (int64_t)sizeof(TS)), smem_addr(&mbar[k % STAGES]));
     };
     // this thread's defect entry of chunk k -> sd[k % (GD + 1)], one commit group per chunk
     auto gather = [&](int64_t k) {
         const int64_t p = (blockIdx.x + k * G) * CP + q;
-        if (k < mine && lane < 27 && p < g.patches) {
+        if (k < mine && lane < 27 && p < npatch) {
             int px, py, pz;
-            patch_xyz(g, p, px, py, pz);
+            patch_xyz(g, ids ? (int64_t)ids[p] : p, px, py, pz);
             const int an = row / NC, c = row - an * NC;
             cp_async_elem(&sd[k % (GD + 1)][q][row], d + patch_node(g, px, py, pz, an) * NC + c);
         }
@@ -145,7 +145,7 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
             return;
         }
         const int64_t p = (blockIdx.x + k * G) * CP + q;
-        if (p < g.patches && lane < 27) {
+        if (p < npatch && lane < 27) {
             const TS* Ap = ring + st * stage_elems + (int64_t)q * stride;
             const T* dk = sd[k % (GD + 1)][q];
             T acc = T(0);
@@ -271,7 +271,8 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
 // resident count comes from the occupancy calculator for the kernel's shared
 // memory (cached per device and kernel instance).
 template <typename T, typename TS, int DIM, int STAGES, int THREADS>
-static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
+static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s,
+                        int64_t npatch, const int32_t* ids) {
     constexpr int CP = (THREADS / 32) / (DIM == 2 ? 1 : 4);
     const size_t smem = (size_t)STAGES * CP * stride * sizeof(TS);
     auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS>;
@@ -287,14 +288,16 @@ static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d
         r = std::max(1, per_sm) * std::max(1, sms);
         if (dev >= 0 && dev < kMaxDevices) resident[dev] = r;
     }
-    const int64_t chunks = (g.patches + CP - 1) / CP;
+    const int64_t chunks = (npatch + CP - 1) / CP;
     const dim3 grid((unsigned)std::min<int64_t>(chunks, r));
-    pdl_launch(kern, grid, dim3(THREADS), smem, s, g, inv, stride, d, corr);
+    pdl_launch(kern, grid, dim3(THREADS), smem, s, g, inv, stride, d, corr, npatch, ids);
 }
 
 template <typename T, typename TS>
-void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s) {
+void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s,
+                        int64_t npatch, const int32_t* ids) {
     g_launches += 1;
+    if (npatch < 0) npatch = g.patches;
     // the bulk copies need 16-byte aligned chunks and the unpadded column
     // layout (stride at most n_p^2 rounded up to 16 bytes); FP64 and other
     // layouts use the warp kernel
@@ -302,27 +305,27 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     const bool lean = g.nc == g.dim;   // n_c = d: warp kernel (the ring's chunks are 27-row slices)
     const bool ring = !lean && sizeof(TS) <= 4 && ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
                       stride >= (int64_t)np * np && stride * (int64_t)sizeof(TS) <= (int64_t)np * np * sizeof(TS) + 16;
-    if (g.patches == 0) return;
+    if (npatch == 0) return;
     if constexpr (sizeof(TS) <= 4) {
         if (ring) {
             // about 70 KB (2d, 3 CTAs per SM) / 187 KB (3d, one CTA per SM) of
             // inverses in flight per CTA; 3d BF16 chunks hold two patches (8
             // warps), so that the apply of a chunk keeps pace with its copy
             constexpr int S2 = sizeof(TS) == 4 ? 6 : 12;
-            if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s);
-            else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s);
-            else launch_ring<T, TS, 3, 4, 256>(g, inv, stride, d, corr, s);
+            if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s, npatch, ids);
+            else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s, npatch, ids);
+            else launch_ring<T, TS, 3, 4, 256>(g, inv, stride, d, corr, s, npatch, ids);
             return;
         }
     }
     constexpr int W = 4;
-    const dim3 grid((unsigned)((g.patches + W - 1) / W));
+    const dim3 grid((unsigned)((npatch + W - 1) / W));
     if (g.dim == 2)
         pdl_launch(lean ? k_vanka_apply<T, TS, 2, W, 2> : k_vanka_apply<T, TS, 2, W, 3>, grid, dim3(W * 32), 0, s, g,
-                   inv, stride, d, corr);
+                   inv, stride, d, corr, npatch, ids);
     else
         pdl_launch(lean ? k_vanka_apply<T, TS, 3, W, 3> : k_vanka_apply<T, TS, 3, W, 4>, grid, dim3(W * 32), 0, s, g,
-                   inv, stride, d, corr);
+                   inv, stride, d, corr, npatch, ids);
 }
 
 template <typename T>
@@ -412,9 +415,12 @@ void launch_convert(const TI* in, TO* out, int64_t n, cudaStream_t s) {
 
 template void launch_spmv<double>(const Geom&, const double*, const double*, const double*, double*, bool, cudaStream_t);
 template void launch_spmv<float>(const Geom&, const float*, const float*, const float*, float*, bool, cudaStream_t);
-template void launch_vanka_apply<double, double>(const Geom&, const double*, int64_t, const double*, double*, cudaStream_t);
-template void launch_vanka_apply<float, float>(const Geom&, const float*, int64_t, const float*, float*, cudaStream_t);
-template void launch_vanka_apply<float, __nv_bfloat16>(const Geom&, const __nv_bfloat16*, int64_t, const float*, float*, cudaStream_t);
+template void launch_vanka_apply<double, double>(const Geom&, const double*, int64_t, const double*, double*, cudaStream_t,
+                                                 int64_t, const int32_t*);
+template void launch_vanka_apply<float, float>(const Geom&, const float*, int64_t, const float*, float*, cudaStream_t,
+                                               int64_t, const int32_t*);
+template void launch_vanka_apply<float, __nv_bfloat16>(const Geom&, const __nv_bfloat16*, int64_t, const float*, float*,
+                                                       cudaStream_t, int64_t, const int32_t*);
 template void launch_vanka_update<double>(const Geom&, const double*, double*, bool, double, bool, cudaStream_t);
 template void launch_vanka_update<float>(const Geom&, const float*, float*, bool, float, bool, cudaStream_t);
 template void launch_restrict<double>(const Geom&, const Geom&, const double*, double*, const uint8_t*, cudaStream_t);

@@ -136,6 +136,9 @@ _SIGS = {
     "nmg_server_memory": [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
     "nmg_set_wait_limit": [_H, C.c_int],
     "nmg_set_lifting_operator": [_H, C.c_int64, C.c_int64, _P, _P, _P, C.c_int],
+    "nmg_set_large_patches": [_H, _P],
+    "nmg_patch_layout": [_H, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                         C.POINTER(C.c_int)],
     "nmg_deformation_update": [_H, _P, _P, C.c_double, _P, _P],
     "nmg_extension_rhs": [_H, _P, _P, _P],
     "nmg_newton_substeps": [_H, _H, _P, _P, C.c_double, _P, _P, _P, _P, C.POINTER(nmg_solve_opts),
@@ -327,3 +330,12 @@ def nmg_jacobian_reuse_time_step(m: nmg_jacobian_reuse) -> int:
 def nmg_jacobian_reuse_decide(m: nmg_jacobian_reuse, residual_inf, assemble: C.c_int) -> int:
     return _lib.nmg_jacobian_reuse_decide(C.byref(m) if m is not None else None, residual_inf,
                                           C.byref(assemble) if assemble is not None else None)
+
+
+def nmg_set_large_patches(h, cell_mask) -> int:
+    return _lib.nmg_set_large_patches(h, ptr(cell_mask))
+
+
+def nmg_patch_layout(h, level, nsmall, nlarge, np_small, np_large) -> int:
+    ref = lambda v: None if v is None else C.byref(v)
+    return _lib.nmg_patch_layout(h, level, ref(nsmall), ref(nlarge), ref(np_small), ref(np_large))

@@ -58,6 +58,17 @@ class Session:
         v = np.ascontiguousarray(vals, dtype=np.float64)
         nmg.check(nmg.nmg_set_jacobian(self.handle, lev, rp.shape[0] - 1, ci.shape[0], rp, ci, v, 0))
 
+    def set_large_patches(self, cell_mask):
+        """Large Vanka patches (4^d cells) over the flagged finest-level cells
+        (numpy array in array order (z,) y, x, i.e. x fastest), or None."""
+        m = None if cell_mask is None else np.ascontiguousarray(cell_mask, dtype=np.uint8)
+        nmg.check(nmg.nmg_set_large_patches(self.handle, m))
+
+    def patch_layout(self, level):
+        ns, nl, ps, pl = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+        nmg.check(nmg.nmg_patch_layout(self.handle, level, ns, nl, ps, pl))
+        return ns.value, nl.value, ps.value, pl.value
+
     def solve(self, b, x, **opts):
         info = nmg.nmg_solve_info()
         st = nmg.nmg_solve(self.handle, b, x, solve_opts(**opts), info)

@@ -56,6 +56,27 @@ def vanka_step_and_bound(inv, dofs, b, x0, d, abs_ax, weight, omega, prec, dim, 
     return x1, bound
 
 
+def vanka_groups_step_and_bound(groups, b, x0, d, abs_ax, weight, omega, prec, dim, nc):
+    """vanka_step_and_bound for patches of several sizes: groups = [(dofs,
+    inverses)] per size; the dot-product length term uses the largest patch."""
+    n_p = max(dofs.shape[1] for dofs, _ in groups)
+    k = 3 ** dim * nc
+    u_s = U_STORE[prec]
+    corr, t1, t2, t3 = (np.zeros_like(x0) for _ in range(4))
+    for dofs, inv in groups:
+        dp = d[dofs]
+        a_inv = np.abs(inv)
+        np.add.at(corr, dofs, np.einsum("pij,pj->pi", inv, dp))
+        np.add.at(t1, dofs, np.einsum("pij,pj->pi", a_inv, np.abs(dp)))
+        np.add.at(t2, dofs, np.einsum("pij,pj->pi", a_inv, (np.abs(b) + abs_ax)[dofs]))
+        per_patch = a_inv.reshape(a_inv.shape[0], -1).max(axis=1) * np.abs(dp).sum(axis=1)
+        np.add.at(t3, dofs, np.repeat(per_patch[:, None], dofs.shape[1], axis=1))
+    x1 = x0 + omega * weight * corr
+    bound = U32 * np.abs(x0) + omega * weight * (
+        (u_s + (n_p + 2 ** dim + 4) * U32) * t1 + (k + 2) * U32 * t2 + E_INV * t3)
+    return x1, bound
+
+
 def to_storage32(a):
     """The FP32 value the test hands to the library, as FP64."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
