@@ -133,6 +133,8 @@ def parse():
                          "cudaProfilerStart and cudaProfilerStop, then exit (for an ncu launch list)")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS),
                     help="cfg2 is the measured workload; the others are for investigation")
+    ap.add_argument("--large-patches", default="none", choices=["none", "solid", "fluid", "all"],
+                    help="Vanka patches of 4^d cells on this region (patch-size study); none: 2^d-cell patches")
     ap.add_argument("--no-large", action="store_true", help="omit the compact 3d 96^3 record")
     ap.add_argument("--no-serving-sample", action="store_true", help="omit the compact serving record")
     ap.add_argument("--serving-sample", type=int, default=300, help="requests of the compact serving record")
@@ -326,6 +328,10 @@ def gpu_arm(args):
     prec_mask = (1 << nmg.NMG_PREC_FP64) | (1 << args.precision)
     S = Session(sysm.problem.dim, sysm.problem.n, [(l.row_ptr, l.col_idx, l.vals) for l in sysm.levels], sysm.dirichlet,
                 precisions=prec_mask, stream=stream.cuda_stream, ncomp=ncomp)
+    if args.large_patches != "none":
+        from gen.q1fsi import solid_cells
+        solid = solid_cells(sysm.problem, sysm.problem.n)
+        S.set_large_patches({"solid": solid, "fluid": ~solid, "all": np.ones_like(solid)}[args.large_patches])
     n = sysm.unknowns
     b = torch.from_numpy(sysm.rhs).cuda()
     x = torch.empty_like(b)
@@ -440,8 +446,11 @@ def gpu_arm(args):
 
     set_ms = _setup_ms(nmg, S, sysm)
     # (the layout study runs before the multi-vector solves: a layout is set before those)
-    sizes = _patch_sizes(args, S, sysm, stream, flush, use_graph) if ncomp == sysm.problem.dim + 1 else None
-    multi = _multi_rhs(args, S, sysm, stream, flush, use_graph) if args.rhs > 0 and args.precision != 0 else None
+    uniform = args.large_patches == "none"
+    sizes = _patch_sizes(args, S, sysm, stream, flush, use_graph) if ncomp == sysm.problem.dim + 1 and uniform \
+        else None
+    multi = _multi_rhs(args, S, sysm, stream, flush, use_graph) if args.rhs > 0 and args.precision != 0 and uniform \
+        else None
 
     ms = statistics.mean(times)
     ms_max, wall_max = max_over_ranks([ms, wall], dist, "cuda")

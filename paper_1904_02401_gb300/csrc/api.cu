@@ -2484,8 +2484,14 @@ static void advance_group(Server* S, Group* G, cudaError_t q, std::vector<Reques
         cudaStreamSynchronize(h->stream) == cudaSuccess && many_flag) {
         cudaMemsetAsync(h->flags + FLAG_MANY, 0, sizeof(int), h->stream);
         fail(NMG_ERR_TIMEOUT, "a bounded device wait of the multi-vector apply ran out");
+        // every column fails; the ones still iterating go straight to their finish (no further
+        // V-cycle or Arnoldi step of a result that is discarded)
         for (int k = 0; k < kMaxCols; ++k)
-            if (G->col[k]) job_fail(G->col[k]->job, NMG_ERR_TIMEOUT);
+            if (Request* r = G->col[k]) {
+                job_fail(r->job, NMG_ERR_TIMEOUT);
+                if (r->job.phase != SolveJob::P_DONE) job_enqueue_finish(r->job);
+            }
+        nw = 0;
     }
     for (int k = 0; k < kMaxCols; ++k)
         if (G->col[k] && G->col[k]->job.phase == SolveJob::P_DONE) finish_grouped(S, G->col[k], active, res);
