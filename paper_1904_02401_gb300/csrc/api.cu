@@ -908,6 +908,7 @@ struct SolveJob {
     Phase phase = P_NONE;
     int its = 0, cycles = 0, engine = NMG_ENGINE_KERNELS;
     bool used_loop = false;
+    bool finish_ready = false;   // the finish copies were enqueued with the last true residual
     double bnorm = 0.0, relres = 0.0;
     nmg_status st = NMG_OK;
     std::string err;
@@ -950,6 +951,18 @@ static void job_enqueue_cycle(SolveJob& J) {
     scale_into_vcycle_input(h, J.o, h->w64, false);
     JOB_CK(cudaMemcpyAsync(h->host_scal, h->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
     J.phase = SolveJob::P_CYCLE;
+}
+
+// The first cycle from x0 = 0: the residual b - A 0 is b itself (bitwise:
+// every product term is a signed zero and b_i - 0 = b_i) and its norm is the
+// ||b|| just computed with the same reduction, so the cycle starts from b
+// without a product and without another host round trip.
+static void job_enqueue_first_cycle(SolveJob& J) {
+    Hierarchy* h = J.h;
+    cudaStream_t s = h->stream;
+    JOB_CK(cudaMemcpyAsync(h->scal + S_BETA, h->scal + S_BNORM, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    launch_start_cycle(h->scal, J.o.restart, h->cyc, s);
+    scale_into_vcycle_input(h, J.o, h->b64, false);
 }
 
 // One FGMRES step j (read on the device from cyc[0]): z_j = M^{-1} v_j (v_j is
@@ -1151,7 +1164,17 @@ static void job_advance(SolveJob& J) {
         } else if (J.bnorm == 0.0) {
             job_enqueue_finish(J);
         } else {
-            job_enqueue_cycle(J);
+            J.relres = 1.0;   // ||b - A 0|| / ||b||
+            if (J.relres <= J.o.rtol) {
+                job_enqueue_finish(J);
+            } else if (J.its >= J.o.maxit) {
+                fail(NMG_ERR_NOT_CONVERGED, "maxit reached");
+                job_fail(J, NMG_ERR_NOT_CONVERGED);
+                job_enqueue_finish(J);
+            } else {
+                job_enqueue_first_cycle(J);
+                if (J.phase != SolveJob::P_DONE) job_enqueue_iter(J);
+            }
         }
         break;
     case SolveJob::P_CYCLE: {
@@ -1162,7 +1185,12 @@ static void job_advance(SolveJob& J) {
             job_fail(J, NMG_ERR_NONFINITE);
             job_enqueue_finish(J);
         } else if (J.relres <= J.o.rtol) {
-            job_enqueue_finish(J);
+            if (J.finish_ready) {   // its copies completed with the residual: read the flags now
+                J.phase = SolveJob::P_FINISH;
+                job_advance(J);
+            } else {
+                job_enqueue_finish(J);
+            }
         } else if (J.its >= J.o.maxit) {
             fail(NMG_ERR_NOT_CONVERGED, "maxit reached");
             job_fail(J, NMG_ERR_NOT_CONVERGED);
@@ -1187,7 +1215,19 @@ static void job_advance(SolveJob& J) {
             const int64_t n = g.nodes * g.nc;
             launch_solve_update(h->scal, k, J.o.restart, h->Z, n, h->x64, n, h->stream);
             ++J.cycles;
+            const bool est_converged = hs[S_EST] <= J.o.rtol;
             job_enqueue_cycle(J);
+            // the estimate says converged: the true residual almost always agrees, so the
+            // result and status copies go with it (one host round trip fewer; repeated
+            // by the finish when the residual disagrees)
+            J.finish_ready = false;
+            if (est_converged && J.phase == SolveJob::P_CYCLE) {
+                job_enqueue_finish(J);
+                if (J.phase == SolveJob::P_FINISH) {
+                    J.phase = SolveJob::P_CYCLE;
+                    J.finish_ready = true;
+                }
+            }
         } else {
             job_enqueue_iter(J);
         }
