@@ -77,7 +77,7 @@ def load_workload(name):
 # capture of the current kernel source (profiles/k_vanka_apply_*.md); a
 # workload or precision without a capture of the current source reports null.
 PROFILED_TRAFFIC = {
-    ("cfg2", 1): 48_783_104 + 7_424,        # k_vanka_apply_ring<float,float,2,6>, 2d 256x256, FP32
+    ("cfg2", 1): 48_787_712 + 7_680,        # k_vanka_apply_ring<float,float,2,6>, 2d 256x256, FP32
     ("cfg3", 1): 191_705_600 + 3_771_648,   # k_vanka_apply_ring<float,float,3,4>, 3d 32^3, FP32
 }
 WORKLOAD = "cfg2"
@@ -425,6 +425,8 @@ def gpu_arm(args):
     # alone: one launch at a time after an L2-evicting write
     cold = cold_launches(nmg, S, sysm, stream, flush, args.precision, 2, args.steps)
     scold = cold_launches(nmg, S, sysm, stream, flush, args.precision, 3, args.steps)
+    plain_apply = plain_read_cold(cold[2], stream, flush, args.steps) if cold[1] else None
+    plain_spmv = plain_read_cold(scold[2], stream, flush, args.steps) if scold[1] else None
     _, _, vprof = timed_solves(args.precision, args.steps, min(use_graph, 1), profile=1)
     rep = C.create_string_buffer(32768)
     nmg.check(nmg.nmg_autotune_report(S.handle, rep, 32768))
@@ -497,7 +499,7 @@ def gpu_arm(args):
                      "bytes_per_launch": kbytes,
                      "timed": f"all {klaunch} launches of {args.steps} plain-launch solves, events around each on "
                               "its stream (the level's data partly L2-resident between smoothing steps)",
-                     "cold": _cold_line(cold, hbm)},
+                     "cold": _cold_line(cold, hbm, plain_apply)},
         "e2e": {"value": statistics.mean(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.launches for i in infos)),
@@ -516,7 +518,7 @@ def gpu_arm(args):
     line["setup"] = _setup_line(sysm, set_ms)
     line["multi_rhs"] = multi
     line["patch_sizes"] = sizes
-    line["spmv"] = dict(_spmv_line(sprof, hbm) or {}, cold=_cold_line(scold, hbm))
+    line["spmv"] = dict(_spmv_line(sprof, hbm) or {}, cold=_cold_line(scold, hbm, plain_spmv))
     if world == 1 and not args.no_serving_sample:
         line["serving"] = _serving_sample(args)
     if world == 1 and not args.no_large and WORKLOAD == "cfg2":
@@ -771,13 +773,43 @@ def _multi_rhs(args, S, sysm, stream, flush, use_graph):
             "vcycle_us_per_column": sig(1000.0 * v_many / K), "single_vcycle_us": sig(1000.0 * v_single)}
 
 
-def _cold_line(prof, hbm):
-    """Rate of launches timed alone after an L2-evicting write (cold_launches)."""
+def plain_read_cold(nbytes, stream, flush, reps):
+    """Microseconds of a plain library read of nbytes (torch.sum over an FP32
+    buffer of that size), timed exactly as cold_launches times a kernel: after
+    the same L2-evicting write, events on the same stream.  It is the rate a
+    memory-bound launch of that size reaches under this timing, for comparison
+    with the copy peak measured on gigabytes."""
+    import torch
+    buf = torch.ones(max(1, int(nbytes) // 4), dtype=torch.float32, device="cuda")
+    out = torch.empty((), dtype=torch.float32, device="cuda")
+    times = []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 2):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.sum(buf, dim=0, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            if r >= 2:
+                times.append(1000.0 * e0.elapsed_time(e1))
+    return sum(times) / len(times)
+
+
+def _cold_line(prof, hbm, plain_us=None):
+    """Rate of launches timed alone after an L2-evicting write (cold_launches),
+    beside a plain read of the same bytes timed the same way."""
     ms, cnt, nbytes = prof
     if not cnt:
         return None
     gbs = nbytes / (ms / cnt * 1e-3) / 1e9
-    return {"us": sig(1000.0 * ms / cnt), "GBps": sig(gbs), "frac": sig(gbs / hbm, 3)}
+    line = {"us": sig(1000.0 * ms / cnt), "GBps": sig(gbs), "frac": sig(gbs / hbm, 3)}
+    if plain_us:
+        line["plain_read"] = {"what": "torch.sum over the same bytes, same timing", "us": sig(plain_us),
+                              "frac": sig(nbytes / (plain_us * 1e-6) / 1e9 / hbm, 3),
+                              "kernel_over_plain": sig(1000.0 * ms / cnt / plain_us, 3)}
+    return line
 
 
 def _spmv_line(prof, hbm):

@@ -104,15 +104,44 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
                   (uint32_t)(cnt * stride * (int64_t)sizeof(TS)), smem_addr(&mbar[k % STAGES]));
     };
     // this thread's defect entry of chunk k -> sd[k % (GD + 1)], one commit group per chunk
+    // The gathers are issued for k = 0, 1, 2, ... in turn.  Without a patch
+    // list the patch of chunk k advances by G CP patches per chunk, so its
+    // coordinates (gx, gy, gz) are stepped with carries instead of divided
+    // out of the index, and this thread's entry of a patch is a fixed offset
+    // (lane_off) from the patch's first node: the per-chunk address work is a
+    // few integer additions on the critical path of every chunk.
+    const int an = row / NC, cc = row - an * NC;
+    const int64_t lane_off =
+        (int64_t)((an % 3) + (int64_t)g.nn[0] * (((an / 3) % 3) + (int64_t)g.nn[1] * (an / 9))) * NC + cc;
+    int gx = 0, gy = 0, gz = 0, sx = 0, sy = 0, sz = 0;
+    if (!ids) {
+        patch_xyz(g, (int64_t)blockIdx.x * CP + q, gx, gy, gz);
+        patch_xyz(g, G * CP, sx, sy, sz);   // the step, as coordinates (G CP < patches)
+    }
     auto gather = [&](int64_t k) {
         const int64_t p = (blockIdx.x + k * G) * CP + q;
         if (k < mine && lane < 27 && p < npatch) {
-            int px, py, pz;
-            patch_xyz(g, ids ? (int64_t)ids[p] : p, px, py, pz);
-            const int an = row / NC, c = row - an * NC;
-            cp_async_elem(&sd[k % (GD + 1)][q][row], d + patch_node(g, px, py, pz, an) * NC + c);
+            int64_t off;
+            if (ids) {
+                int px, py, pz;
+                patch_xyz(g, (int64_t)ids[p], px, py, pz);
+                off = patch_node(g, px, py, pz, an) * NC + cc;
+            } else {
+                off = (2 * (int64_t)gx + (int64_t)g.nn[0] * (2 * (int64_t)gy + (int64_t)g.nn[1] * 2 * gz)) * NC +
+                      lane_off;
+            }
+            cp_async_elem(&sd[k % (GD + 1)][q][row], d + off);
         }
         cp_async_commit();
+        if (!ids) {   // on to the patch of chunk k + 1 (sx < pc0, sy < pc1: one carry each)
+            gx += sx;
+            const int cx = gx >= g.pc[0];
+            gx -= cx ? g.pc[0] : 0;
+            gy += sy + cx;
+            const int cy = gy >= g.pc[1];
+            gy -= cy ? g.pc[1] : 0;
+            gz += sz + cy;
+        }
     };
     if (tid == 0)
         for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(&mbar[st]));
