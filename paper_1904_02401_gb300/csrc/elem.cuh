@@ -175,12 +175,30 @@ __device__ __forceinline__ void spmv_node(const Geom& g, const T* __restrict__ A
     spmv_node_f<T, DIM, decltype(xval)&, GLOBAL_A, GB, NC>(g, A, xval, b, y, residual, i);
 }
 
+// The NC values of node block j of x: with VEC (NC = 4, x 16-byte aligned)
+// one float4 or two double2 loads instead of NC scalar loads.
+template <typename T, int NC, bool VEC>
+__device__ __forceinline__ void load_xblock(const T* __restrict__ xj, T (&xv)[NC]) {
+    if constexpr (VEC && NC == 4 && sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(xj);
+        xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+    } else if constexpr (VEC && NC == 4 && sizeof(T) == 8) {
+        const double2 v0 = reinterpret_cast<const double2*>(xj)[0];
+        const double2 v1 = reinterpret_cast<const double2*>(xj)[1];
+        xv[0] = v0.x; xv[1] = v0.y; xv[2] = v1.x; xv[3] = v1.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xv[c] = xj[c];
+    }
+}
+
 // Row r of node i of y = A x or b - A x: the same terms in the same order as
 // row r of spmv_node (stencil positions ascending, then block columns), so the
 // value is bitwise equal; lets a kernel spread a node's rows over threads.
 // In 2d the loads of the 9 stencil positions are issued before their
-// products (in 3d one position at a time measured faster).
-template <typename T, int DIM, int NC = DIM + 1>
+// products (in 3d one position at a time measured faster).  VEC: x blocks
+// are read with vector loads (NC = 4 and x 16-byte aligned; same values).
+template <typename T, int DIM, int NC = DIM + 1, bool VEC = false>
 __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A, const T* __restrict__ x,
                                          const T* __restrict__ b, T* __restrict__ y, bool residual, int64_t i,
                                          int r) {
@@ -200,8 +218,10 @@ __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A,
             if (ok) {
                 const int64_t j = i + dx + dy * sy + dz * sz;
                 const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
+                T xv[NC];
+                load_xblock<T, NC, VEC>(x + j * NC, xv);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), x[j * NC + c], acc);
+                for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), xv[c], acc);
             }
         }
         y[i * NC + r] = residual ? b[i * NC + r] - acc : acc;

@@ -37,7 +37,7 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
 // where a node's row work is long (3d: 108 terms per row; FP64), slower for
 // the 2d FP32 product, whose extra reads of x cost more than the added
 // parallelism gains.
-template <typename T, int DIM, int NC = DIM + 1>
+template <typename T, int DIM, int NC = DIM + 1, bool VEC = false>
 __global__ void __launch_bounds__(256, 1)
 k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
             T* __restrict__ y, bool residual) {
@@ -45,7 +45,7 @@ k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* _
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= g.nodes * NC) return;
     const uint32_t nodes = (uint32_t)g.nodes, r = (uint32_t)t / nodes;
-    spmv_row<T, DIM, NC>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
+    spmv_row<T, DIM, NC, VEC>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
 }
 
 // corr_i = A_i^{-1} R_i d for every patch i: one warp per patch.  The patch
@@ -285,7 +285,11 @@ template <typename T>
 void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual, cudaStream_t s) {
     g_launches += 1;
     const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
-    if (g.dim == 3)
+    // 3d with 4 unknowns a node: a node block of x is 16 or 32 aligned bytes (vector loads)
+    if (g.dim == 3 && !lean && (uintptr_t)x % 16 == 0)
+        pdl_launch(k_spmv_rows<T, 3, 4, true>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y,
+                   residual);
+    else if (g.dim == 3)
         pdl_launch(lean ? k_spmv_rows<T, 3, 3> : k_spmv_rows<T, 3, 4>, dim3(blocks_for(g.nodes * g.nc, 256)),
                    dim3(256), 0, s, g, A, x, b, y, residual);
     else if constexpr (sizeof(T) == 8)
