@@ -1007,9 +1007,9 @@ static void enqueue_arnoldi(Hierarchy* h, const nmg_solve_opts& o, bool in_loop,
     launch_gs_update_dot_norm(h->V, n, h->cyc, h->w64, n, h->partial, h->scal, m, h->counters, s);
     Level& F = h->lev[h->L - 1];
     if (o.precision == NMG_PREC_FP64)
-        launch_gs_update_scale<double>(h->V, n, h->cyc, h->scal, h->w64, (double*)F.p[NMG_PREC_FP64].b, n, s);
+        launch_gs_update_scale<double>(h->V, n, h->cyc, h->scal, h->w64, (double*)F.p[NMG_PREC_FP64].b, n, m, s);
     else
-        launch_gs_update_scale<float>(h->V, n, h->cyc, h->scal, h->w64, (float*)F.p[o.precision].b, n, s);
+        launch_gs_update_scale<float>(h->V, n, h->cyc, h->scal, h->w64, (float*)F.p[o.precision].b, n, m, s);
     launch_decide(h->scal, h->cyc, o.rtol, o.maxit, m, loop, in_loop, s);
 }
 

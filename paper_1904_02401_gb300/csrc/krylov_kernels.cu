@@ -54,10 +54,11 @@ k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ pa
 
 // Column j of the Hessenberg matrix from the two Gram-Schmidt passes
 // (coefficients scal[S_HC + i] + scal[S_Y + i], i <= j) and h_{j+1,j} = hnext:
-// apply the earlier rotations, build rotation j, update g, write the residual
-// estimate |g_{j+1}| / ||b|| and 1 / h_{j+1,j}.  Called by a whole block: the
-// inputs are first staged in shared memory by all threads (one memory latency
+// apply the earlier rotations, build rotation j, update g and write the
+// residual estimate |g_{j+1}| / ||b||.  Called by a whole block: the inputs
+// are first staged in shared memory by all threads (one memory latency
 // instead of one per rotation), then thread 0 runs the serial recurrence.
+// The other threads return at once.
 __device__ void arnoldi_column(double* scal, int j, int m, double hnext) {
     __shared__ double sH[kMaxRestart + 2], scs[kMaxRestart], ssn[kMaxRestart];
     __shared__ double sg, sbn;
@@ -92,7 +93,6 @@ __device__ void arnoldi_column(double* scal, int j, int m, double hnext) {
     scal[S_G + j] = c * sg;
     const double est = fabs(-s * sg) / sbn;
     scal[S_EST] = est;
-    scal[S_INVH] = hnext != 0.0 ? 1.0 / hnext : 0.0;
     if (!isfinite(est) || !isfinite(hnext)) scal[S_STATUS] = (double)NMG_ERR_NONFINITE;
     scal[S_ITER] += 1.0;
 }
@@ -150,20 +150,32 @@ inline unsigned grid_for(int64_t n) {
 }
 
 
-// Sum over the kDotBlocks partials of row k in the fixed order of
-// k_finish_dots (lane-strided, then a shuffle tree); valid in lane 0.  The
-// loads of a lane are issued together (one memory latency per row).
-__device__ __forceinline__ double finish_row(const double* __restrict__ partial, int k, int lane) {
-    constexpr int R = (kDotBlocks + 31) / 32;
-    double v[R];
+// v[0] + ... + v[N-1] as a fixed pairwise tree (ceil(log2 N) dependent
+// additions instead of N - 1: on GB300 a dependent FP64 addition costs tens of
+// cycles, and these sums sit on the serial tail of the Arnoldi step).
+template <int N>
+__device__ __forceinline__ double tree_sum(double (&v)[N]) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int w = 1; w < N; w *= 2)
+#pragma unroll
+        for (int u = 0; u + w < N; u += 2 * w) v[u] += v[u + w];
+    return v[0];
+}
+
+// The kDotBlocks partials of row k, lane-strided: lane l loads blocks l,
+// l + 32, ... (all its loads issued together); row_sum then adds them.
+constexpr int kRowPer = (kDotBlocks + 31) / 32;
+__device__ __forceinline__ void load_row(const double* __restrict__ partial, int k, int lane, double (&v)[kRowPer]) {
+#pragma unroll
+    for (int r = 0; r < kRowPer; ++r) {
         const int b = lane + 32 * r;
         v[r] = b < kDotBlocks ? __ldcg(partial + (int64_t)k * kDotBlocks + b) : 0.0;
     }
-    double s = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) s += v[r];
+}
+// Sum of the loaded row: each lane's values as a tree, then a shuffle tree;
+// valid in lane 0.
+__device__ __forceinline__ double row_sum(double (&v)[kRowPer]) {
+    double s = tree_sum<kRowPer>(v);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     return s;
 }
@@ -239,10 +251,10 @@ __device__ __forceinline__ void block_partials(double (&acc)[W], double* __restr
     if (lane < W) red[warp][lane] = v;
     __syncthreads();
     if (warp == 0 && lane < W) {
-        double t = red[0][lane];
+        double f[kMdWarps];
 #pragma unroll
-        for (int ww = 1; ww < kMdWarps; ++ww) t += red[ww][lane];
-        partial[((int64_t)chunk * gridDim.x + blockIdx.x) * kMdChunk + lane] = t;
+        for (int ww = 0; ww < kMdWarps; ++ww) f[ww] = red[ww][lane];
+        partial[((int64_t)chunk * gridDim.x + blockIdx.x) * kMdChunk + lane] = tree_sum<kMdWarps>(f);
     }
     __syncthreads();
 }
@@ -294,14 +306,17 @@ __device__ __forceinline__ void dots_all(const double* __restrict__ V, int64_t l
 }
 
 // In the last block: out[k] = sum over the blocks of the partials of value k
-// (warp w sums the blocks w, w + kMdWarps, ..., then the warps are added).
-// Launched on kDotBlocks blocks: a lane's loads are all issued before they are
-// summed (one memory round trip for the whole tail).
-__device__ void finish_chunks(const double* __restrict__ partial, int nvec, double* __restrict__ out, int lane,
-                              int warp) {
+// (warp w sums the blocks w, w + kMdWarps, ... as a tree, then the warps'
+// sums are added as a tree).  Launched on kDotBlocks blocks: a lane's loads
+// are all issued before they are summed (one memory round trip for the whole
+// tail).  Returns, in lane l of warp 0, the sum of out[k]^2 over k = l,
+// l + 32, ... (fma in ascending k), for ||out||^2.
+__device__ double finish_chunks(const double* __restrict__ partial, int nvec, double* __restrict__ out, int lane,
+                                int warp) {
     __shared__ double fs[kMdWarps][kMdChunk];
     constexpr int G = kDotBlocks;
     constexpr int PER = (G + kMdWarps - 1) / kMdWarps;
+    double sq = 0.0;
     for (int c0 = 0, chunk = 0; c0 < nvec; c0 += kMdChunk, ++chunk) {
         const double* p = partial + (int64_t)chunk * G * kMdChunk + lane;
         double v[PER];
@@ -310,19 +325,19 @@ __device__ void finish_chunks(const double* __restrict__ partial, int nvec, doub
             const int b = warp + u * kMdWarps;
             v[u] = b < G ? __ldcg(p + (int64_t)b * kMdChunk) : 0.0;
         }
-        double s = 0.0;
-#pragma unroll
-        for (int u = 0; u < PER; ++u) s += v[u];
-        fs[warp][lane] = s;
+        fs[warp][lane] = tree_sum<PER>(v);
         __syncthreads();
         if (warp == 0 && c0 + lane < nvec) {
-            double t = fs[0][lane];
+            double f[kMdWarps];
 #pragma unroll
-            for (int ww = 1; ww < kMdWarps; ++ww) t += fs[ww][lane];
+            for (int ww = 0; ww < kMdWarps; ++ww) f[ww] = fs[ww][lane];
+            const double t = tree_sum<kMdWarps>(f);
             out[c0 + lane] = t;
+            sq = fma(t, t, sq);
         }
         __syncthreads();
     }
+    return sq;
 }
 
 // Outer product of step j = cyc[0] fused with the first Gram-Schmidt pass:
@@ -364,8 +379,9 @@ k_spmv_zstore_dots(Geom g, const double* __restrict__ A, const TX* __restrict__ 
 // w <- w - sum_k h1_k V_k (h1 = scal[S_HC..], the first pass), ||w||^2 and
 // h2_k = V_k . w (into scal[S_Y..]); then, in the last block,
 // h_{j+1,j} = ||w - V h2|| = sqrt(||w||^2 - ||h2||^2) (Pythagoras: the V_k
-// are orthonormal, as in low-synchronisation CGS2) and the Givens update of
-// column j.  Each thread reads back only the elements it wrote.
+// are orthonormal, as in low-synchronisation CGS2) and its reciprocal, which
+// the next kernel scales by.  Each thread reads back only the elements it
+// wrote.  The Givens update of column j runs in the next kernel.
 __global__ void __launch_bounds__(kMdThreads)
 k_gs_update_dot_norm(const double* __restrict__ V, int64_t ldv, const int* __restrict__ cyc, double* w, int64_t n,
                      double* __restrict__ partial, double* scal, int m, unsigned* counter) {
@@ -391,43 +407,49 @@ k_gs_update_dot_norm(const double* __restrict__ V, int64_t ldv, const int* __res
     if (lane == 0) red[warp] = ww;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = red[0];
+        double f[kMdWarps];
 #pragma unroll
-        for (int k = 1; k < kMdWarps; ++k) t += red[k];
-        partial[(int64_t)kNormRow * kDotBlocks + blockIdx.x] = t;
+        for (int k = 0; k < kMdWarps; ++k) f[k] = red[k];
+        partial[(int64_t)kNormRow * kDotBlocks + blockIdx.x] = tree_sum<kMdWarps>(f);
     }
     dots_all(V, ldv, nvec, w, lo, hi, partial, lane, warp);
     if (!last_block(counter)) return;
-    finish_chunks(partial, nvec, scal + S_Y, lane, warp);   // ends with a block barrier
+    // warp 0's loads of the ||w||^2 partials are in flight while the chunks are summed
+    double nrow[kRowPer];
+    if (warp == 0) load_row(partial, kNormRow, lane, nrow);
+    // h2 into scal[S_Y..]; lane l of warp 0 gets h2_l^2 + h2_{l+32}^2 (ascending k)
+    double hh = finish_chunks(partial, nvec, scal + S_Y, lane, warp);   // ends with a block barrier
     if (warp == 0) {
-        const double t = finish_row(partial, kNormRow, lane);
-        // ||h2||^2 by the warp: lane l squares h2_l and h2_{l+32}, then a fixed shuffle tree
-        double hh = 0.0;
-        for (int k = lane; k < nvec; k += 32) hh = fma(scal[S_Y + k], scal[S_Y + k], hh);
+        const double t = row_sum(nrow);
+        // ||h2||^2: the lanes' squares added by a fixed shuffle tree
         for (int off = 16; off > 0; off >>= 1) hh += __shfl_down_sync(0xffffffffu, hh, off);
         if (lane == 0) {
             const double d = t - hh;
             s_hnext = d > 0.0 ? sqrt(d) : 0.0;
             scal[S_HC + j + 1] = s_hnext;
+            scal[S_INVH] = s_hnext != 0.0 ? 1.0 / s_hnext : 0.0;
         }
     }
-    __syncthreads();
-    arnoldi_column(scal, j, m, s_hnext);
+    (void)m;
 }
 
 // Second update fused with the scaling: v_{j+1} = (w - sum_k h2_k V_k) *
 // scal[S_INVH] into basis column j + 1 and, converted, into vin (the
-// right-hand side of the next V-cycle).
+// right-hand side of the next V-cycle).  Block 0 also runs the Givens update
+// of column j (arnoldi_column): a serial chain of dependent FP64 operations
+// (about 8 us on GB300) that only the decision after this kernel needs, so
+// it overlaps the streaming update instead of delaying it.
 template <typename TV>
 __global__ void __launch_bounds__(kThreads)
-k_gs_update_scale(double* V, int64_t ldv, const int* __restrict__ cyc, const double* __restrict__ scal,
-                  const double* __restrict__ w, TV* __restrict__ vin, int64_t n) {
+k_gs_update_scale(double* V, int64_t ldv, const int* __restrict__ cyc, double* scal,
+                  const double* __restrict__ w, TV* __restrict__ vin, int64_t n, int m) {
     NMG_PDL_ENTRY();
     __shared__ double hs[kMaxRestart + 1];
     const int j = cyc[0], nvec = j + 1;
     for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = scal[S_Y + k];
     __syncthreads();
     const double a = scal[S_INVH];
+    if (blockIdx.x == 0) arnoldi_column(scal, j, m, scal[S_HC + j + 1]);
     double* y = V + (int64_t)(j + 1) * ldv;
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         double v = w[i];
@@ -525,15 +547,15 @@ void launch_gs_update_dot_norm(const double* V, int64_t ldv, const int* cyc, dou
 }
 
 template <typename TV>
-void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, const double* scal, const double* w, TV* vin,
-                            int64_t n, cudaStream_t s) {
+void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, double* scal, const double* w, TV* vin,
+                            int64_t n, int m, cudaStream_t s) {
     g_launches += 1;
-    pdl_launch(k_gs_update_scale<TV>, dim3(grid_for(n)), dim3(kThreads), 0, s, V, ldv, cyc, scal, w, vin, n);
+    pdl_launch(k_gs_update_scale<TV>, dim3(grid_for(n)), dim3(kThreads), 0, s, V, ldv, cyc, scal, w, vin, n, m);
 }
-template void launch_gs_update_scale<float>(double*, int64_t, const int*, const double*, const double*, float*,
-                                            int64_t, cudaStream_t);
-template void launch_gs_update_scale<double>(double*, int64_t, const int*, const double*, const double*, double*,
-                                             int64_t, cudaStream_t);
+template void launch_gs_update_scale<float>(double*, int64_t, const int*, double*, const double*, float*,
+                                            int64_t, int, cudaStream_t);
+template void launch_gs_update_scale<double>(double*, int64_t, const int*, double*, const double*, double*,
+                                             int64_t, int, cudaStream_t);
 
 template <typename TV>
 void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,

@@ -324,13 +324,14 @@ template <typename TX>
 void launch_spmv_zstore_dots(const Geom& g, const double* A, const TX* xf, double* Z, double* w, const double* V,
                              int64_t ldv, const int* cyc, double* partial, double* out, unsigned* counter,
                              cudaStream_t s);
-// w -= V scal[S_HC..]; scal[S_Y..] = V^T w; h_{j+1,j} and the Givens update of column j.
+// w -= V scal[S_HC..]; scal[S_Y..] = V^T w; h_{j+1,j} and its reciprocal.
 void launch_gs_update_dot_norm(const double* V, int64_t ldv, const int* cyc, double* w, int64_t n, double* partial,
                                double* scal, int m, unsigned* counter, cudaStream_t s);
-// V_{j+1} = (w - V scal[S_Y..]) * scal[S_INVH], also converted into vin.
+// V_{j+1} = (w - V scal[S_Y..]) * scal[S_INVH], also converted into vin; the
+// Givens update of column j of the Hessenberg matrix (restart length m).
 template <typename TV>
-void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, const double* scal, const double* w, TV* vin,
-                            int64_t n, cudaStream_t s);
+void launch_gs_update_scale(double* V, int64_t ldv, const int* cyc, double* scal, const double* w, TV* vin,
+                            int64_t n, int m, cudaStream_t s);
 template <typename TV>
 void launch_scale_convert(const double* x, const double* scal_ptr, double* V, int64_t ldv, const int* cyc, bool next,
                           TV* vin, int64_t n, cudaStream_t s);

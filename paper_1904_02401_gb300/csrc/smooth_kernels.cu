@@ -87,9 +87,12 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
     constexpr int RW = NP / 27;                    // warps per patch
     constexpr int CP = (THREADS / 32) / RW;   // patches per chunk
     constexpr int GD = kGatherDepth;
+    static_assert(sizeof(T) == 4, "the streaming apply computes in FP32");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[STAGES];
-    __shared__ T sd[GD + 1][CP][NP];
+    // a patch's defect row padded to a whole number of 16-byte units: read back as float4
+    constexpr int NPD = (NP + 3) / 4 * 4;
+    __shared__ __align__(16) T sd[GD + 1][CP][NPD];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int q = w / RW, row = (w % RW) * 27 + lane;
@@ -176,10 +179,17 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
         const int64_t p = (blockIdx.x + k * G) * CP + q;
         if (p < npatch && lane < 27) {
             const TS* Ap = ring + st * stage_elems + (int64_t)q * stride;
-            const T* dk = sd[k % (GD + 1)][q];
+            // the patch's defect (a broadcast to every lane) in NPD / 4 vector loads
+            T dv[NPD];
+            const float4* d4 = reinterpret_cast<const float4*>(sd[k % (GD + 1)][q]);
+#pragma unroll
+            for (int u = 0; u < NPD / 4; ++u) {
+                const float4 v = d4[u];
+                dv[4 * u] = v.x; dv[4 * u + 1] = v.y; dv[4 * u + 2] = v.z; dv[4 * u + 3] = v.w;
+            }
             T acc = T(0);
 #pragma unroll
-            for (int j = 0; j < NP; ++j) acc = fma(Cvt<T, TS>::f(Ap[j * NP + row]), dk[j], acc);
+            for (int j = 0; j < NP; ++j) acc = fma(Cvt<T, TS>::f(Ap[j * NP + row]), dv[j], acc);
             corr[p * NP + row] = acc;
         }
         __syncthreads();   // stage st and the defect slot of chunk k are free again
