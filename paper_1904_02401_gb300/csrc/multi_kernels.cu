@@ -82,6 +82,25 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
     blk /= tiles_x;
     const int by = blk % tiles_y, bz = blk / tiles_y;
     const int x0 = bx * TX - 1, y0 = by * TY - 1, z0 = DIM == 3 ? bz * TZ - 1 : 0;
+    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int ix = x0 + 1 + tx, iy = y0 + 1 + ty, iz = DIM == 3 ? z0 + 1 + tz : 0;
+    const bool inside = ix < g.nn[0] && iy < g.nn[1] && iz < g.nn[2];
+    const int64_t i = inside ? ix + (int64_t)g.nn[0] * (iy + (int64_t)g.nn[1] * iz) : 0;
+    // The matrix blocks of three stencil positions at a time.  The first group
+    // is loaded before the wait for the kernel that produces X (the matrix does
+    // not change during a solve).  In 2d each next group is loaded while the
+    // current one is summed (two buffers); in 3d the second buffer's registers
+    // would cost a CTA per SM, so a group is loaded when it is reached.
+    constexpr bool PIPE = DIM == 2;
+    float av[PIPE ? 2 : 1][3][NB];
+    auto load_group = [&](float (&dst)[3][NB], int s0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int e = 0; e < NB; ++e)
+                dst[q][e] = inside ? __ldg(A + ((int64_t)(s0 + q) * NB + e) * g.ld + i) : 0.f;
+    };
+    load_group(av[0], 0);
     NMG_PDL_ENTRY();
     for (int t = threadIdx.x; t < HX * HY * HZ * NQ; t += TX * TY * TZ) {
         const int hn = t / NQ, q = t - hn * NQ;
@@ -91,11 +110,8 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
             xs4[hn * (NS / 4) + q] = ld4(x + (gx + (int64_t)g.nn[0] * (gy + (int64_t)g.nn[1] * gz)) * NV + 4 * q);
     }
     __syncthreads();
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
-    const int ix = x0 + 1 + tx, iy = y0 + 1 + ty, iz = DIM == 3 ? z0 + 1 + tz : 0;
     const int hz0 = DIM == 3 ? tz + 1 : 0;   // the node's own plane in the halo tile
-    if (ix >= g.nn[0] || iy >= g.nn[1] || iz >= g.nn[2]) return;
-    const int64_t i = ix + (int64_t)g.nn[0] * (iy + (int64_t)g.nn[1] * iz);
+    if (!inside) return;
     float acc[NC][K];
 #pragma unroll
     for (int r = 0; r < NC; ++r)
@@ -103,11 +119,12 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
         for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
 #pragma unroll
     for (int s0 = 0; s0 < NST; s0 += 3) {
-        float av[3][NB];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int e = 0; e < NB; ++e) av[q][e] = __ldg(A + ((int64_t)(s0 + q) * NB + e) * g.ld + i);
+        const int cur = PIPE ? (s0 / 3) & 1 : 0;
+        if constexpr (PIPE) {
+            if (s0 + 3 < NST) load_group(av[cur ^ 1], s0 + 3);
+        } else {
+            if (s0 > 0) load_group(av[0], s0);
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const int s = s0 + q;
@@ -123,7 +140,7 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
 #pragma unroll
                     for (int r = 0; r < NC; ++r)
 #pragma unroll
-                        for (int k = 0; k < K; ++k) acc[r][k] = fmaf(av[q][r * NC + c], xv[k], acc[r][k]);
+                        for (int k = 0; k < K; ++k) acc[r][k] = fmaf(av[cur][q][r * NC + c], xv[k], acc[r][k]);
                 }
             }
         }
