@@ -233,6 +233,75 @@ k_prolong_residual(Geom f, Geom c, const T* __restrict__ A, const T* __restrict_
     if (i < f.nodes) prolong_residual_node<T, DIM>(f, c, A, ec, x_in, fmask, b, x_out, r, i);
 }
 
+// Fused Vanka update (MODE 0) or prolongation (MODE 1) and residual on a 2d
+// tile: the CTA computes the new iterate on its TX x TY nodes and their
+// one-node halo into shared memory (its own nodes also into x_out), then
+// r = b - A x_new for its nodes from shared memory.  The node's matrix blocks
+// are loaded into registers before the wait for the previous kernel (the
+// matrix does not change during a solve).  A value is computed once per tile
+// (the halo adds a ring of neighbours), by the element functions of the
+// separate kernels, and the residual sums in spmv_node's order, so the results
+// equal the separate kernels' bit for bit.  x_out must not alias x_in.
+template <typename T, int MODE, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 2)
+k_update_residual_tile(Geom g, Geom gc, const T* __restrict__ A, const T* __restrict__ src, const T* __restrict__ x_in,
+                       bool x_zero, T omega, bool average, const uint8_t* __restrict__ fmask, const T* __restrict__ b,
+                       T* __restrict__ x_out, T* __restrict__ r) {
+    constexpr int NC = 3, NB = NC * NC, HX = TX + 2, HY = TY + 2;
+    __shared__ T xs[HX * HY * NC];
+    const int tiles_x = (g.nn[0] + TX - 1) / TX;
+    const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+    const int x0 = bx * TX - 1, y0 = by * TY - 1;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int ix = x0 + 1 + tx, iy = y0 + 1 + ty;
+    const bool inside = ix < g.nn[0] && iy < g.nn[1];
+    const int64_t i = inside ? ix + (int64_t)g.nn[0] * iy : 0;
+    // the node's blocks of the 9 stencil positions (present in the stencil
+    // layout for every position, zero outside the mesh)
+    T av[9][NB];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int e = 0; e < NB; ++e) av[q][e] = inside ? __ldg(A + ((int64_t)q * NB + e) * g.ld + i) : T(0);
+    NMG_PDL_ENTRY();
+    T bv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) bv[c] = inside ? b[i * NC + c] : T(0);
+    for (int t = threadIdx.x; t < HX * HY; t += TX * TY) {
+        const int hx = t % HX, hy = t / HX;
+        const int gx = x0 + hx, gy = y0 + hy;
+        if (gx >= 0 && gx < g.nn[0] && gy >= 0 && gy < g.nn[1]) {
+            const int64_t j = gx + (int64_t)g.nn[0] * gy;
+            T v[NC];
+            if constexpr (MODE == 0) vanka_update_value<T, 2>(g, src, x_in, x_zero, omega, average, j, v);
+            else prolong_value<T, 2>(g, gc, src, x_in, fmask, j, v);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) xs[t * NC + c] = v[c];
+            if (hx >= 1 && hx <= TX && hy >= 1 && hy <= TY)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) x_out[j * NC + c] = v[c];
+        }
+    }
+    __syncthreads();
+    if (!inside) return;
+    T acc[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] = T(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int dx = q % 3 - 1, dy = q / 3 - 1;
+        if (ix + dx >= 0 && ix + dx < g.nn[0] && iy + dy >= 0 && iy + dy < g.nn[1]) {
+            const T* xn = xs + ((tx + 1 + dx) + HX * (ty + 1 + dy)) * NC;
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[k] = fma(av[q][k * NC + c], xn[c], acc[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) r[i * NC + k] = bv[k] - acc[k];
+}
+
 // r_c = P^T r_f (Q1 full weighting), coarse Dirichlet entries zero.  One thread per coarse node.
 template <typename T, int DIM, int NC = DIM + 1>
 __global__ void __launch_bounds__(256, 1)
@@ -390,11 +459,24 @@ void launch_vanka_update2(const Geom& g, const T* corr, const T* x_in, T* x_out,
                    x_zero, omega, average);
 }
 
+// 2d FP32 tiles of 32 x 8 nodes (one thread a node).
+constexpr int kUrTx = 32, kUrTy = 8;
+inline unsigned ur_tiles(const Geom& g) {
+    return (unsigned)(((g.nn[0] + kUrTx - 1) / kUrTx) * ((g.nn[1] + kUrTy - 1) / kUrTy));
+}
+
 template <typename T>
 void launch_update_residual(const Geom& g, const T* A, const T* corr, const T* x_in, bool x_zero, T omega,
                             bool average, const T* b, T* x_out, T* r, cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(g.nodes, 256));
+    if constexpr (sizeof(T) == 4) {
+        if (g.dim == 2 && g.nc == 3) {
+            pdl_launch(k_update_residual_tile<T, 0, kUrTx, kUrTy>, dim3(ur_tiles(g)), dim3(kUrTx * kUrTy), 0, s, g, g,
+                       A, corr, x_in, x_zero, omega, average, (const uint8_t*)nullptr, b, x_out, r);
+            return;
+        }
+    }
     if (g.dim == 2)
         pdl_launch(k_update_residual<T, 2>, grid, dim3(256), 0, s, g, A, corr, x_in, x_zero, omega, average, b, x_out, r);
     else
@@ -406,6 +488,13 @@ void launch_prolong_residual(const Geom& f, const Geom& c, const T* A, const T* 
                              const uint8_t* fmask, const T* b, T* x_out, T* r, cudaStream_t s) {
     g_launches += 1;
     const dim3 grid(blocks_for(f.nodes, 256));
+    if constexpr (sizeof(T) == 4) {
+        if (f.dim == 2 && f.nc == 3) {
+            pdl_launch(k_update_residual_tile<T, 1, kUrTx, kUrTy>, dim3(ur_tiles(f)), dim3(kUrTx * kUrTy), 0, s, f, c,
+                       A, ec, x_in, false, T(0), false, fmask, b, x_out, r);
+            return;
+        }
+    }
     if (f.dim == 2) pdl_launch(k_prolong_residual<T, 2>, grid, dim3(256), 0, s, f, c, A, ec, x_in, fmask, b, x_out, r);
     else pdl_launch(k_prolong_residual<T, 3>, grid, dim3(256), 0, s, f, c, A, ec, x_in, fmask, b, x_out, r);
 }
