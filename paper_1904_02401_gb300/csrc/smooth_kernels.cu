@@ -78,14 +78,15 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 // and there is no tail wave.  Row i of a patch is summed over the columns j in
 // ascending order with one fma per term, as in apply_patch, so the
 // corrections equal those of the other apply kernels bit for bit.
-template <typename T, typename TS, int DIM, int STAGES, int THREADS>
+template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1>
 __global__ void __launch_bounds__(THREADS, 1)
 k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
                    T* __restrict__ corr, int64_t npatch, const int32_t* __restrict__ ids) {
     constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     constexpr int RW = NP / 27;                    // warps per patch
-    constexpr int CP = (THREADS / 32) / RW;   // patches per chunk
+    static_assert(PW == 1 || RW == 1, "two patches a warp only for 27-row patches");
+    constexpr int CP = (THREADS / 32) / RW * PW;   // patches per chunk (PW patches per warp)
     constexpr int GD = kGatherDepth;
     static_assert(sizeof(T) == 4, "the streaming apply computes in FP32");
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -95,7 +96,7 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
     __shared__ __align__(16) T sd[GD + 1][CP][NPD];
     TS* ring = reinterpret_cast<TS*>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int q = w / RW, row = (w % RW) * 27 + lane;
+    const int q0 = (w / RW) * PW, row = (w % RW) * 27 + lane;   // the warp's patches q0 .. q0 + PW - 1
     const int64_t G = gridDim.x;
     const int64_t nchunks = (npatch + CP - 1) / CP;
     const int64_t mine = (nchunks - blockIdx.x + G - 1) / G;   // the grid is at most nchunks
@@ -116,35 +117,40 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
     const int an = row / NC, cc = row - an * NC;
     const int64_t lane_off =
         (int64_t)((an % 3) + (int64_t)g.nn[0] * (((an / 3) % 3) + (int64_t)g.nn[1] * (an / 9))) * NC + cc;
-    int gx = 0, gy = 0, gz = 0, sx = 0, sy = 0, sz = 0;
+    int gx[PW] = {}, gy[PW] = {}, gz[PW] = {}, sx = 0, sy = 0, sz = 0;
     if (!ids) {
-        patch_xyz(g, (int64_t)blockIdx.x * CP + q, gx, gy, gz);
+#pragma unroll
+        for (int t = 0; t < PW; ++t) patch_xyz(g, (int64_t)blockIdx.x * CP + q0 + t, gx[t], gy[t], gz[t]);
         patch_xyz(g, G * CP, sx, sy, sz);   // the step, as coordinates (G CP < patches)
     }
     auto gather = [&](int64_t k) {
-        const int64_t p = (blockIdx.x + k * G) * CP + q;
-        if (k < mine && lane < 27 && p < npatch) {
-            int64_t off;
-            if (ids) {
-                int px, py, pz;
-                patch_xyz(g, (int64_t)ids[p], px, py, pz);
-                off = patch_node(g, px, py, pz, an) * NC + cc;
-            } else {
-                off = (2 * (int64_t)gx + (int64_t)g.nn[0] * (2 * (int64_t)gy + (int64_t)g.nn[1] * 2 * gz)) * NC +
-                      lane_off;
+#pragma unroll
+        for (int t = 0; t < PW; ++t) {
+            const int64_t p = (blockIdx.x + k * G) * CP + q0 + t;
+            if (k < mine && lane < 27 && p < npatch) {
+                int64_t off;
+                if (ids) {
+                    int px, py, pz;
+                    patch_xyz(g, (int64_t)ids[p], px, py, pz);
+                    off = patch_node(g, px, py, pz, an) * NC + cc;
+                } else {
+                    off = (2 * (int64_t)gx[t] + (int64_t)g.nn[0] * (2 * (int64_t)gy[t] + (int64_t)g.nn[1] * 2 * gz[t])) *
+                              NC +
+                          lane_off;
+                }
+                cp_async_elem(&sd[k % (GD + 1)][q0 + t][row], d + off);
             }
-            cp_async_elem(&sd[k % (GD + 1)][q][row], d + off);
+            if (!ids) {   // on to the patch of chunk k + 1 (sx < pc0, sy < pc1: one carry each)
+                gx[t] += sx;
+                const int cx = gx[t] >= g.pc[0];
+                gx[t] -= cx ? g.pc[0] : 0;
+                gy[t] += sy + cx;
+                const int cy = gy[t] >= g.pc[1];
+                gy[t] -= cy ? g.pc[1] : 0;
+                gz[t] += sz + cy;
+            }
         }
         cp_async_commit();
-        if (!ids) {   // on to the patch of chunk k + 1 (sx < pc0, sy < pc1: one carry each)
-            gx += sx;
-            const int cx = gx >= g.pc[0];
-            gx -= cx ? g.pc[0] : 0;
-            gy += sy + cx;
-            const int cy = gy >= g.pc[1];
-            gy -= cy ? g.pc[1] : 0;
-            gz += sz + cy;
-        }
     };
     if (tid == 0)
         for (int st = 0; st < STAGES; ++st) mbar_init(smem_addr(&mbar[st]));
@@ -176,21 +182,30 @@ k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* 
             }
             return;
         }
-        const int64_t p = (blockIdx.x + k * G) * CP + q;
-        if (p < npatch && lane < 27) {
-            const TS* Ap = ring + st * stage_elems + (int64_t)q * stride;
-            // the patch's defect (a broadcast to every lane) in NPD / 4 vector loads
-            T dv[NPD];
-            const float4* d4 = reinterpret_cast<const float4*>(sd[k % (GD + 1)][q]);
+        const int64_t p0 = (blockIdx.x + k * G) * CP + q0;
+        if (lane < 27) {
+            // the warp's PW patches side by side (independent sums); a patch's
+            // defect (a broadcast to every lane) in NPD / 4 vector loads
+            T dv[PW][NPD], acc[PW];
 #pragma unroll
-            for (int u = 0; u < NPD / 4; ++u) {
-                const float4 v = d4[u];
-                dv[4 * u] = v.x; dv[4 * u + 1] = v.y; dv[4 * u + 2] = v.z; dv[4 * u + 3] = v.w;
+            for (int t = 0; t < PW; ++t) {
+                const float4* d4 = reinterpret_cast<const float4*>(sd[k % (GD + 1)][q0 + t]);
+#pragma unroll
+                for (int u = 0; u < NPD / 4; ++u) {
+                    const float4 v = d4[u];
+                    dv[t][4 * u] = v.x; dv[t][4 * u + 1] = v.y; dv[t][4 * u + 2] = v.z; dv[t][4 * u + 3] = v.w;
+                }
+                acc[t] = T(0);
             }
-            T acc = T(0);
+            const TS* Ap = ring + st * stage_elems + (int64_t)q0 * stride;
 #pragma unroll
-            for (int j = 0; j < NP; ++j) acc = fma(Cvt<T, TS>::f(Ap[j * NP + row]), dv[j], acc);
-            corr[p * NP + row] = acc;
+            for (int j = 0; j < NP; ++j)
+#pragma unroll
+                for (int t = 0; t < PW; ++t)
+                    acc[t] = fma(Cvt<T, TS>::f(Ap[(int64_t)t * stride + j * NP + row]), dv[t][j], acc[t]);
+#pragma unroll
+            for (int t = 0; t < PW; ++t)
+                if (p0 + t < npatch) corr[(p0 + t) * NP + row] = acc[t];
         }
         __syncthreads();   // stage st and the defect slot of chunk k are free again
         if (tid == 0 && k + STAGES < mine) issue(k + STAGES);
@@ -382,12 +397,12 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
 // Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
 // resident count comes from the occupancy calculator for the kernel's shared
 // memory (cached per device and kernel instance).
-template <typename T, typename TS, int DIM, int STAGES, int THREADS>
+template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1>
 static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s,
                         int64_t npatch, const int32_t* ids) {
-    constexpr int CP = (THREADS / 32) / (DIM == 2 ? 1 : 4);
+    constexpr int CP = (THREADS / 32) / (DIM == 2 ? 1 : 4) * PW;
     const size_t smem = (size_t)STAGES * CP * stride * sizeof(TS);
-    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS>;
+    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS, PW>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     static int resident[kMaxDevices] = {};
     int dev = 0;
@@ -423,8 +438,14 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
             // about 70 KB (2d, 3 CTAs per SM) / 187 KB (3d, one CTA per SM) of
             // inverses in flight per CTA; 3d BF16 chunks hold two patches (8
             // warps), so that the apply of a chunk keeps pace with its copy
+            // 2d: on levels of at least 4096 patches two patches a warp (chunks of 8,
+            // 3 (FP32) or 6 (BF16) stages): half the chunk rounds a CTA walks, each
+            // with its fixed cost of barriers, waits and copy issue; smaller levels
+            // keep one patch a warp (twice the CTAs for their latency-bound steps)
             constexpr int S2 = sizeof(TS) == 4 ? 6 : 12;
-            if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s, npatch, ids);
+            if (g.dim == 2 && npatch >= 4096)
+                launch_ring<T, TS, 2, S2 / 2, 128, 2>(g, inv, stride, d, corr, s, npatch, ids);
+            else if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s, npatch, ids);
             else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s, npatch, ids);
             else launch_ring<T, TS, 3, 4, 256>(g, inv, stride, d, corr, s, npatch, ids);
             return;
