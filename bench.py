@@ -77,7 +77,7 @@ def load_workload(name):
 # capture of the current kernel source (profiles/k_vanka_apply_*.md); a
 # workload or precision without a capture of the current source reports null.
 PROFILED_TRAFFIC = {
-    ("cfg2", 1): 48_787_712 + 7_680,        # k_vanka_apply_ring<float,float,2,6>, 2d 256x256, FP32
+    ("cfg2", 1): 48_786_944 + 44_544,       # k_vanka_apply_ring<float,float,2,3,128,2>, 2d 256x256, FP32
     ("cfg3", 1): 191_705_600 + 3_771_648,   # k_vanka_apply_ring<float,float,3,4>, 3d 32^3, FP32
 }
 WORKLOAD = "cfg2"
