@@ -125,6 +125,29 @@ def test_vcycle_every_entry(full, prec, use_graph):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
+def test_engines_agree_at_full_size(full, prec):
+    """At this size the streaming apply runs its wrapping ring and, on the 2d
+    levels of at least 4096 patches, two patches a warp; the per-step kernels
+    (plain and replayed as a graph) and the persistent engine (its own
+    double-buffered apply) sum the same terms in the same order, so their
+    V-cycles agree bit for bit."""
+    from paper_1904_02401_gb300 import nmg
+    from paper_1904_02401_gb300.session import solve_opts
+    name, s, h, S, stream = full
+    r = _f32(to_storage32(s.rhs))
+    outs = []
+    for engine, graph in ((nmg.NMG_ENGINE_KERNELS, 0), (nmg.NMG_ENGINE_KERNELS, 1), (nmg.NMG_ENGINE_PERSISTENT, 0)):
+        z = torch.zeros_like(r)
+        with torch.cuda.stream(stream):
+            nmg.check(nmg.nmg_vcycle(S.handle, solve_opts(precision=prec, use_graph=graph, engine=engine), r, z))
+        stream.synchronize()
+        outs.append(z)
+    assert torch.isfinite(outs[0]).all()
+    for k in range(1, len(outs)):
+        assert torch.equal(outs[0], outs[k]), k
+
+
+@pytest.mark.parametrize("prec", [1, 2])
 def test_vcycle_many_columns_every_entry(full, prec):
     """Columns 0 and 5 of an 8-column multi-vector V-cycle against the oracle."""
     from paper_1904_02401_gb300 import nmg
