@@ -70,8 +70,9 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 
 // Streaming apply for FP32 / BF16 inverses (2d and 3d): a persistent grid of
 // a few CTAs per SM walks the chunks c = blockIdx.x + k * gridDim.x; a chunk
-// is one patch per warp in 2d, or one patch per 4 warps (27 rows each) in 3d,
-// i.e. THREADS / 32 x 27 rows.  Each CTA keeps STAGES chunk copies
+// is PW patches per warp in 2d (a lane sums row `lane` of each, the PW sums
+// side by side), or one patch per 4 warps (27 rows each) in 3d.  Each CTA
+// keeps STAGES chunk copies
 // of inverses (TMA bulk copies completing on one mbarrier per stage) and the
 // defect gathers of kGatherDepth chunks (cp.async) in flight, so neither the
 // DRAM queue nor the gather latency depends on how many warps are resident,
