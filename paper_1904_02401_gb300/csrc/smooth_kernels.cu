@@ -436,9 +436,12 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     if (npatch == 0) return;
     if constexpr (sizeof(TS) <= 4) {
         if (ring) {
-            // about 70 KB (2d, 3 CTAs per SM) / 187 KB (3d, one CTA per SM) of
-            // inverses in flight per CTA; 3d BF16 chunks hold two patches (8
-            // warps), so that the apply of a chunk keeps pace with its copy
+            // 2d: about 70 KB of inverses in flight per CTA, 3 CTAs per SM.
+            // 3d: one 108-unknown patch a chunk (4 warps), 3 stages of FP32
+            // (140 KB, one CTA per SM) or 4 of BF16 (93 KB, two CTAs per SM): the
+            // shared memory left free lets the next kernel's CTAs start while this
+            // one drains (4 stages of FP32, or BF16 chunks of two patches, measured
+            // slower in the solve).
             // 2d: on levels of at least 4096 patches two patches a warp (chunks of 8,
             // 3 (FP32) or 6 (BF16) stages): half the chunk rounds a CTA walks, each
             // with its fixed cost of barriers, waits and copy issue; smaller levels
@@ -447,8 +450,8 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
             if (g.dim == 2 && npatch >= 4096)
                 launch_ring<T, TS, 2, S2 / 2, 128, 2>(g, inv, stride, d, corr, s, npatch, ids);
             else if (g.dim == 2) launch_ring<T, TS, 2, S2, 128>(g, inv, stride, d, corr, s, npatch, ids);
-            else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s, npatch, ids);
-            else launch_ring<T, TS, 3, 4, 256>(g, inv, stride, d, corr, s, npatch, ids);
+            else if (sizeof(TS) == 4) launch_ring<T, TS, 3, 3, 128>(g, inv, stride, d, corr, s, npatch, ids);
+            else launch_ring<T, TS, 3, 4, 128>(g, inv, stride, d, corr, s, npatch, ids);
             return;
         }
     }
