@@ -78,7 +78,7 @@ def load_workload(name):
 # workload or precision without a capture of the current source reports null.
 PROFILED_TRAFFIC = {
     ("cfg2", 1): 48_786_944 + 44_544,       # k_vanka_apply_ring<float,float,2,3,128,2>, 2d 256x256, FP32
-    ("cfg3", 1): 191_705_600 + 3_771_648,   # k_vanka_apply_ring<float,float,3,4>, 3d 32^3, FP32
+    ("cfg3", 1): 191_715_072 + 4_028_672,   # k_vanka_apply_ring<float,float,3,3,128,1>, 3d 32^3, FP32
 }
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
