@@ -36,9 +36,13 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
 // segment of each stencil array while a node's rows run in parallel.  Faster
 // where a node's row work is long (3d: 108 terms per row; FP64), slower for
 // the 2d FP32 product, whose extra reads of x cost more than the added
-// parallelism gains.
+// parallelism gains.  A thread keeps only one stencil position's 4 loads in
+// flight, so the 3d FP32 product needs many resident warps: it is held to 32
+// registers (8 CTAs, 64 warps per SM; 40 registers gave 6 CTAs and a 96^3
+// product 15% slower).  FP64 keeps the compiler's choice (capping it at 40
+// registers made the 3d 32^3 FP64 solve 3% slower).
 template <typename T, int DIM, int NC = DIM + 1, bool VEC = false>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, (DIM == 3 && sizeof(T) == 4) ? 8 : 1)
 k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
             T* __restrict__ y, bool residual) {
     NMG_PDL_ENTRY();
