@@ -124,7 +124,8 @@ struct ResidentVCycle {
     __device__ void residual(const RLevel& L) {
         int64_t lo, hi;
         own_range(L.g.nodes, L.node_chunk, rank, lo, hi);
-        const T* As = vec(L.o_A) - lo;   // owned rows, indexed by the global node
+        // owned rows, indexed by the global node (the layout's node stride is 1 in 2d, NB in 3d)
+        const T* As = vec(L.o_A) - lo * (DIM == 3 ? NC * NC : 1);
         for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
             spmv_node<T, DIM, T, false>(L.gA, As, vec(L.o_x), vec(L.o_b), vec(L.o_r), true, i);
         publish(L.o_r, lo * NC, hi * NC);
@@ -235,17 +236,20 @@ struct ResidentVCycle {
             const uint32_t cnt = (uint32_t)(hi - lo);
             const T* A = reinterpret_cast<const T*>(L.A);
             if (cnt > 0) {
-                // As[s * node_chunk + j] = A[s * ld + lo + j], s < NA, j < cnt
+                // the owned nodes' entries, in the stencil layout with ld = node_chunk:
+                // As[stencil_off(nch, s, e, j)] = A[stencil_off(ld, s, e, lo + j)],
+                // a = s * NB + e < NA, j < cnt
+                constexpr int NB = NC * NC;
                 const int nch = L.node_chunk;
                 const int64_t ld = L.g.ld;
                 stage(vec(L.o_A), (int64_t)NA * cnt,
                       [&](int64_t k) {
-                          const uint32_t s = (uint32_t)k / cnt;
-                          return A[s * ld + lo + ((uint32_t)k - s * cnt)];
+                          const uint32_t a = (uint32_t)k / cnt, j = (uint32_t)k - a * cnt;
+                          return A[stencil_off<DIM, NB>(ld, (int)(a / NB), (int)(a % NB), lo + j)];
                       },
                       [&](int64_t k) {
-                          const uint32_t s = (uint32_t)k / cnt;
-                          return (int64_t)s * nch + ((uint32_t)k - s * cnt);
+                          const uint32_t a = (uint32_t)k / cnt, j = (uint32_t)k - a * cnt;
+                          return stencil_off<DIM, NB>(nch, (int)(a / NB), (int)(a % NB), (int64_t)j);
                       });
             }
             int64_t plo, phi;

@@ -42,6 +42,31 @@ __device__ __forceinline__ double widen_exact(float f) {
 template <typename T, typename TX> __device__ __forceinline__ T widen(TX v) { return (T)v; }
 template <> __device__ __forceinline__ double widen<double, float>(float v) { return widen_exact(v); }
 
+// N consecutive matrix entries at Ab (3d stencil layout: a node's block of
+// one position, or one row of it): float4 loads when N is a multiple of 4
+// (FP32), double2 loads when N is even (FP64), else entry by entry.  The 3d
+// layout keeps such runs 16-byte aligned (cudaMalloc'd base, blocks of 16
+// entries, rows of 4).
+template <typename T, int N>
+__device__ __forceinline__ void load_arun(const T* __restrict__ Ab, T (&av)[N]) {
+    if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(Ab) + q);
+            av[4 * q] = v.x; av[4 * q + 1] = v.y; av[4 * q + 2] = v.z; av[4 * q + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(Ab) + q);
+            av[2 * q] = v.x; av[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) av[e] = __ldg(Ab + e);
+    }
+}
+
 template <typename TS> __device__ __forceinline__ TS ldg(const TS* p) { return __ldg(p); }
 template <> __device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16* p) { return *p; }
 
@@ -106,17 +131,27 @@ __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ 
                 const int64_t j = i + dx + dy * sy + dz * sz;
                 T xv[NC];
                 xval(j, dx, dy, dz, xv);
-                const T* As = A + (int64_t)s * NB * g.ld + i;
+                const T* As = A + stencil_off<DIM, NB>(g.ld, s, 0, i);
+                if constexpr (DIM == 3 && GLOBAL_A) {   // the node's block: one contiguous segment
+                    T av[NB];
+                    load_arun<T, NB>(As, av);
 #pragma unroll
-                for (int r = 0; r < NC; ++r)
+                    for (int r = 0; r < NC; ++r)
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const T* a = As + (int64_t)(r * NC + c) * g.ld;
-                        T av;
-                        if constexpr (GLOBAL_A) av = __ldg(a);
-                        else av = *a;
-                        acc[r] = fma(av, xv[c], acc[r]);
-                    }
+                        for (int c = 0; c < NC; ++c) acc[r] = fma(av[r * NC + c], xv[c], acc[r]);
+                } else {
+                    const int64_t es = stencil_estride<DIM>(g.ld);
+#pragma unroll
+                    for (int r = 0; r < NC; ++r)
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            const T* a = As + (int64_t)(r * NC + c) * es;
+                            T av;
+                            if constexpr (GLOBAL_A) av = __ldg(a);
+                            else av = *a;
+                            acc[r] = fma(av, xv[c], acc[r]);
+                        }
+                }
             }
         }
         return;
@@ -134,11 +169,12 @@ __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ 
             okv[q] = ok;
             const int64_t j = ok ? i + dx + dy * sy + dz * sz : i;
             xval(j, ok ? dx : 0, ok ? dy : 0, ok ? dz : 0, xv[q]);
-            const T* As = A + (int64_t)s * NB * g.ld + i;
+            const T* As = A + stencil_off<DIM, NB>(g.ld, s, 0, i);
+            const int64_t es = stencil_estride<DIM>(g.ld);
 #pragma unroll
             for (int e = 0; e < NB; ++e) {
-                if constexpr (GLOBAL_A) av[q][e] = __ldg(As + (int64_t)e * g.ld);
-                else av[q][e] = As[(int64_t)e * g.ld];
+                if constexpr (GLOBAL_A) av[q][e] = __ldg(As + (int64_t)e * es);
+                else av[q][e] = As[(int64_t)e * es];
             }
         }
 #pragma unroll
@@ -217,11 +253,18 @@ __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A,
                             (iz + dz >= 0) && (iz + dz < g.nn[2]);
             if (ok) {
                 const int64_t j = i + dx + dy * sy + dz * sz;
-                const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
+                const T* As = A + stencil_off<DIM, NB>(g.ld, s, r * NC, i);
                 T xv[NC];
                 load_xblock<T, NC, VEC>(x + j * NC, xv);
+                if constexpr (DIM == 3) {   // the row's NC entries are contiguous (vector loads for NC = 4)
+                    T av[NC];
+                    load_arun<T, NC>(As, av);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), xv[c], acc);
+                    for (int c = 0; c < NC; ++c) acc = fma(av[c], xv[c], acc);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc = fma(__ldg(As + (int64_t)c * g.ld), xv[c], acc);
+                }
             }
         }
         y[i * NC + r] = residual ? b[i * NC + r] - acc : acc;
@@ -239,10 +282,11 @@ __device__ __forceinline__ void spmv_row(const Geom& g, const T* __restrict__ A,
                             (iz + dz >= 0) && (iz + dz < g.nn[2]);
             okv[q] = ok;
             const int64_t j = ok ? i + dx + dy * sy + dz * sz : i;
-            const T* As = A + ((int64_t)s * NB + r * NC) * g.ld + i;
+            const T* As = A + stencil_off<DIM, NB>(g.ld, s, r * NC, i);
+            const int64_t es = stencil_estride<DIM>(g.ld);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                av[q][c] = __ldg(As + (int64_t)c * g.ld);
+                av[q][c] = __ldg(As + (int64_t)c * es);
                 xv[q][c] = x[j * NC + c];
             }
         }

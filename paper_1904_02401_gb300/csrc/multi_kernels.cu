@@ -95,10 +95,18 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
     float av[PIPE ? 2 : 1][3][NB];
     auto load_group = [&](float (&dst)[3][NB], int s0) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 3; ++q) {
+            if constexpr (DIM == 3) {   // the node's block of one position: one contiguous segment
+                if (inside) elem::load_arun<float, NB>(A + stencil_off<DIM, NB>(g.ld, s0 + q, 0, i), dst[q]);
+                else
 #pragma unroll
-            for (int e = 0; e < NB; ++e)
-                dst[q][e] = inside ? __ldg(A + ((int64_t)(s0 + q) * NB + e) * g.ld + i) : 0.f;
+                    for (int e = 0; e < NB; ++e) dst[q][e] = 0.f;
+            } else {
+#pragma unroll
+                for (int e = 0; e < NB; ++e)
+                    dst[q][e] = inside ? __ldg(A + stencil_off<DIM, NB>(g.ld, s0 + q, e, i)) : 0.f;
+            }
+        }
     };
     load_group(av[0], 0);
     NMG_PDL_ENTRY();

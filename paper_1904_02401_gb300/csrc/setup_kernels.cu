@@ -48,7 +48,7 @@ __global__ void k_bsr_to_stencil(Geom g, const int64_t* __restrict__ rp,
         for (int e = 0; e < nb; ++e) {
             double v = vals[k * nb + e];
             if (!isfinite(v)) atomicOr(&flags[FLAG_NONFINITE], 1);
-            A[((int64_t)s * nb + e) * g.ld + i] = v;
+            A[stencil_off(g.dim, nb, g.ld, s, e, i)] = v;
         }
     }
 }
@@ -163,7 +163,7 @@ k_patch_invert(Geom g, const double* __restrict__ A, double* inv64, int64_t s64,
                 const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
                 const int64_t node = (int64_t)(2 * px + ax) +
                                      (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
-                v = A[((int64_t)s * NC * NC + r * NC + c) * g.ld + node];
+                v = A[stencil_off<DIM, NC * NC>(g.ld, s, r * NC + c, node)];
             }
             a[row * LDA + cl] = v;
         }
@@ -223,7 +223,7 @@ k_patch_invert_large(Geom g, const double* __restrict__ A, const int32_t* __rest
                 const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
                 const int64_t node = (int64_t)(2 * px + ax) +
                                      (int64_t)g.nn[0] * ((2 * py + ay) + (int64_t)g.nn[1] * (2 * pz + az));
-                v = A[((int64_t)s * NC * NC + r * NC + c) * g.ld + node];
+                v = A[stencil_off<DIM, NC * NC>(g.ld, s, r * NC + c, node)];
             }
             a[(int64_t)row * LDA + cl] = v;
         }
@@ -258,7 +258,7 @@ __global__ void k_coarse_assemble(Geom g, const double* __restrict__ A, double* 
         const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
         if (jx < 0 || jx >= g.nn[0] || jy < 0 || jy >= g.nn[1] || jz < 0 || jz >= g.nn[2]) continue;
         const int64_t j = jx + (int64_t)g.nn[0] * (jy + (int64_t)g.nn[1] * jz);
-        D[(i * nc + r) * n + j * nc + c] = A[((int64_t)s * nc * nc + e) * g.ld + i];
+        D[(i * nc + r) * n + j * nc + c] = A[stencil_off(g.dim, nc * nc, g.ld, s, e, i)];
     }
 }
 

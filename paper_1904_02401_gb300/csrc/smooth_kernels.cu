@@ -31,16 +31,18 @@ k_spmv(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __rest
     if (i < g.nodes) spmv_node<T, DIM, T, true, 0, NC>(g, A, x, b, y, residual, i);
 }
 
-// The same product with one thread per (block row, node): thread t computes
-// row r = t / nodes of node t % nodes, so a warp still reads one contiguous
-// segment of each stencil array while a node's rows run in parallel.  Faster
-// where a node's row work is long (3d: 108 terms per row; FP64), slower for
-// the 2d FP32 product, whose extra reads of x cost more than the added
-// parallelism gains.  A thread keeps only one stencil position's 4 loads in
-// flight, so the 3d FP32 product needs many resident warps: it is held to 32
-// registers (8 CTAs, 64 warps per SM; 40 registers gave 6 CTAs and a 96^3
-// product 15% slower).  FP64 keeps the compiler's choice (capping it at 40
-// registers made the 3d 32^3 FP64 solve 3% slower).
+// The same product with one thread per (block row, node).  2d: thread t
+// computes row r = t / nodes of node t % nodes, so a warp reads one contiguous
+// segment of each stencil array.  3d: thread t computes row t % NC of node
+// t / NC, so a warp's loads of one stencil position (the rows of 8
+// consecutive nodes) are one contiguous range of the 3d layout.  Faster where
+// a node's row work is long (3d: 108 terms per row; FP64), slower for the 2d
+// FP32 product, whose extra reads of x cost more than the added parallelism
+// gains.  A thread keeps only one stencil position's loads in flight, so the
+// 3d FP32 product needs many resident warps: it is held to 32 registers (8
+// CTAs, 64 warps per SM; 40 registers gave 6 CTAs and a 96^3 product 15%
+// slower).  FP64 keeps the compiler's choice (capping it at 40 registers made
+// the 3d 32^3 FP64 solve 3% slower).
 template <typename T, int DIM, int NC = DIM + 1, bool VEC = false>
 __global__ void __launch_bounds__(256, (DIM == 3 && sizeof(T) == 4) ? 8 : 1)
 k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* __restrict__ b,
@@ -48,8 +50,13 @@ k_spmv_rows(Geom g, const T* __restrict__ A, const T* __restrict__ x, const T* _
     NMG_PDL_ENTRY();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= g.nodes * NC) return;
-    const uint32_t nodes = (uint32_t)g.nodes, r = (uint32_t)t / nodes;
-    spmv_row<T, DIM, NC, VEC>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
+    if constexpr (DIM == 3) {
+        const uint32_t i = (uint32_t)t / NC;
+        spmv_row<T, DIM, NC, VEC>(g, A, x, b, y, residual, (int64_t)i, (int)((uint32_t)t - i * NC));
+    } else {
+        const uint32_t nodes = (uint32_t)g.nodes, r = (uint32_t)t / nodes;
+        spmv_row<T, DIM, NC, VEC>(g, A, x, b, y, residual, (int64_t)((uint32_t)t - r * nodes), (int)r);
+    }
 }
 
 // corr_i = A_i^{-1} R_i d for every patch i: one warp per patch.  The patch
