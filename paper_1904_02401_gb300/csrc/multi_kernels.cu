@@ -47,24 +47,29 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
 }
 
 // y = A X or y = B - A X for K columns (stencil layout of A as in k_spmv),
-// one thread per node, with X staged in shared memory: a CTA owns a TX x TY
-// (x TZ) tile of nodes and first copies the K-column values of the tile and
-// its one-node halo (coalesced 16-byte loads), so each node's values cross
-// from L2 about once per tile instead of once per neighbour.  A node's K
-// interleaved columns are 12-32 floats, so one thread per node reading them
-// directly from global memory touches a different 128-byte line per lane;
-// from the padded shared-memory slots the reads are conflict-free.  A is read
-// with a warp covering rows of TX consecutive nodes, the blocks of three
-// stencil positions (one x-row of neighbours) loaded together (every
-// position's block exists in the stencil layout, zero outside the mesh).  Per
-// column and row: stencil positions ascending, block columns ascending, one
-// fma per term, as spmv_node / spmv_row.
-template <int DIM, int NC, int K, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ)
+// NC / RS threads per node (each RS of the node's block rows), with X staged
+// in shared memory: a CTA owns a TX x TY (x TZ) tile of nodes and first
+// copies the K-column values of the tile and its one-node halo (coalesced
+// 16-byte loads), so each node's values cross from L2 about once per tile
+// instead of once per neighbour.  A node's K interleaved columns are 12-32
+// floats, so one thread per node reading them directly from global memory
+// touches a different 128-byte line per lane; from the padded shared-memory
+// slots the reads are conflict-free.  A is read with a warp covering rows of
+// consecutive nodes (in 3d the threads of one node take consecutive lanes and
+// their rows are consecutive 32-byte parts of the node's 64-byte block), the
+// blocks of three stencil positions (one x-row of neighbours) loaded together
+// (every position's block exists in the stencil layout, zero outside the
+// mesh).  Per column and row: stencil positions ascending, block columns
+// ascending, one fma per term, as spmv_node / spmv_row.
+template <int DIM, int NC, int K, int TX, int TY, int TZ, int RS = NC>
+__global__ void __launch_bounds__(TX * TY * TZ * (NC / RS))
 k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ x, const float* __restrict__ b,
                  float* __restrict__ y, bool residual) {
     constexpr int NB = NC * NC;
     constexpr int NST = DIM == 2 ? 9 : 27;
+    constexpr int H = NC / RS;      // threads per node
+    constexpr int NT = TX * TY * TZ * H;
+    constexpr int NR = RS * NC;     // matrix entries of a thread's rows per position
     constexpr int HX = TX + 2, HY = TY + 2, HZ = DIM == 3 ? TZ + 2 : 1;
     constexpr int NV = NC * K;      // floats per node
     constexpr int NQ = NV / 4;      // float4 per node
@@ -74,6 +79,7 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
     // in the same 4 banks)
     constexpr int NS = (NQ % 2) ? NV : NV + 4;
     static_assert(DIM == 3 || TZ == 1, "2d tiles are one node deep");
+    static_assert(NC % RS == 0 && (RS == NC || DIM == 3), "a node's rows split over threads in 3d only");
     extern __shared__ float4 xs4[];
     const float* xs = reinterpret_cast<const float*>(xs4);
     const int tiles_x = (g.nn[0] + TX - 1) / TX, tiles_y = (g.nn[1] + TY - 1) / TY;
@@ -82,35 +88,36 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
     blk /= tiles_x;
     const int by = blk % tiles_y, bz = blk / tiles_y;
     const int x0 = bx * TX - 1, y0 = by * TY - 1, z0 = DIM == 3 ? bz * TZ - 1 : 0;
-    const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
+    const int nl = threadIdx.x / H, r0 = (threadIdx.x - nl * H) * RS;   // tile node, first row
+    const int tx = nl % TX, ty = (nl / TX) % TY, tz = nl / (TX * TY);
     const int ix = x0 + 1 + tx, iy = y0 + 1 + ty, iz = DIM == 3 ? z0 + 1 + tz : 0;
     const bool inside = ix < g.nn[0] && iy < g.nn[1] && iz < g.nn[2];
     const int64_t i = inside ? ix + (int64_t)g.nn[0] * (iy + (int64_t)g.nn[1] * iz) : 0;
-    // The matrix blocks of three stencil positions at a time.  The first group
+    // The matrix rows of three stencil positions at a time.  The first group
     // is loaded before the wait for the kernel that produces X (the matrix does
     // not change during a solve).  In 2d each next group is loaded while the
     // current one is summed (two buffers); in 3d the second buffer's registers
     // would cost a CTA per SM, so a group is loaded when it is reached.
     constexpr bool PIPE = DIM == 2;
-    float av[PIPE ? 2 : 1][3][NB];
-    auto load_group = [&](float (&dst)[3][NB], int s0) {
+    float av[PIPE ? 2 : 1][3][NR];
+    auto load_group = [&](float (&dst)[3][NR], int s0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if constexpr (DIM == 3) {   // the node's block of one position: one contiguous segment
-                if (inside) elem::load_arun<float, NB>(A + stencil_off<DIM, NB>(g.ld, s0 + q, 0, i), dst[q]);
+            if constexpr (DIM == 3) {   // the thread's rows of the node's block: one contiguous run
+                if (inside) elem::load_arun<float, NR>(A + stencil_off<DIM, NB>(g.ld, s0 + q, r0 * NC, i), dst[q]);
                 else
 #pragma unroll
-                    for (int e = 0; e < NB; ++e) dst[q][e] = 0.f;
+                    for (int e = 0; e < NR; ++e) dst[q][e] = 0.f;
             } else {
 #pragma unroll
-                for (int e = 0; e < NB; ++e)
+                for (int e = 0; e < NR; ++e)
                     dst[q][e] = inside ? __ldg(A + stencil_off<DIM, NB>(g.ld, s0 + q, e, i)) : 0.f;
             }
         }
     };
     load_group(av[0], 0);
     NMG_PDL_ENTRY();
-    for (int t = threadIdx.x; t < HX * HY * HZ * NQ; t += TX * TY * TZ) {
+    for (int t = threadIdx.x; t < HX * HY * HZ * NQ; t += NT) {
         const int hn = t / NQ, q = t - hn * NQ;
         const int hx = hn % HX, hy = (hn / HX) % HY, hz = hn / (HX * HY);
         const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
@@ -120,9 +127,9 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
     __syncthreads();
     const int hz0 = DIM == 3 ? tz + 1 : 0;   // the node's own plane in the halo tile
     if (!inside) return;
-    float acc[NC][K];
+    float acc[RS][K];
 #pragma unroll
-    for (int r = 0; r < NC; ++r)
+    for (int r = 0; r < RS; ++r)
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
 #pragma unroll
@@ -146,7 +153,7 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
                     float xv[K];
                     ldk<K>(xn + c * K, xv);
 #pragma unroll
-                    for (int r = 0; r < NC; ++r)
+                    for (int r = 0; r < RS; ++r)
 #pragma unroll
                         for (int k = 0; k < K; ++k) acc[r][k] = fmaf(av[cur][q][r * NC + c], xv[k], acc[r][k]);
                 }
@@ -154,18 +161,19 @@ k_spmv_many_tile(Geom g, const float* __restrict__ A, const float* __restrict__ 
         }
     }
 #pragma unroll
-    for (int r = 0; r < NC; ++r) {
+    for (int r = 0; r < RS; ++r) {
         float out[K];
+        const int64_t row = i * NC + r0 + r;
         if (residual) {
             float bv[K];
-            ldk<K>(b + (i * NC + r) * K, bv);
+            ldk<K>(b + row * K, bv);
 #pragma unroll
             for (int k = 0; k < K; ++k) out[k] = bv[k] - acc[r][k];
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k) out[k] = acc[r][k];
         }
-        stk<K>(y + (i * NC + r) * K, out);
+        stk<K>(y + row * K, out);
     }
 }
 
@@ -562,28 +570,29 @@ void apply_many_dispatch(const Geom& g, const TS* inv, int64_t stride, const flo
         }                                                                \
     } while (0)
 
-template <int DIM, int NC, int K, int TX, int TY, int TZ>
+template <int DIM, int NC, int K, int TX, int TY, int TZ, int RS = NC>
 static void launch_spmv_many_tile(const Geom& g, const float* A, const float* x, const float* b, float* y,
                                   bool residual, cudaStream_t s) {
     constexpr int NV = NC * K, NS = ((NV / 4) % 2) ? NV : NV + 4;
     const size_t smem = (size_t)(TX + 2) * (TY + 2) * (DIM == 3 ? TZ + 2 : 1) * NS * sizeof(float);
-    auto kern = k_spmv_many_tile<DIM, NC, K, TX, TY, TZ>;
+    auto kern = k_spmv_many_tile<DIM, NC, K, TX, TY, TZ, RS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const unsigned tiles = (unsigned)(((g.nn[0] + TX - 1) / TX) * ((g.nn[1] + TY - 1) / TY) *
                                       (DIM == 3 ? (g.nn[2] + TZ - 1) / TZ : 1));
-    pdl_launch(kern, dim3(tiles), dim3(TX * TY * TZ), smem, s, g, A, x, b, y, residual);
+    pdl_launch(kern, dim3(tiles), dim3(TX * TY * TZ * (NC / RS)), smem, s, g, A, x, b, y, residual);
 }
 
-// Tiles of 128 threads: 3d 16 x 4 x 2 nodes (about 150 registers, three CTAs
-// per SM; a warp's matrix loads cover two 64-byte row segments), 2d 32 x 4
-// nodes.
+// Tiles of 3d 16 x 4 x 2 nodes and 2d 32 x 4 nodes.  With 4 unknowns a node
+// (3d) two threads share a node, two block rows each (256 threads): a thread
+// then holds 16 accumulators and 24 prefetched matrix entries instead of 32
+// and 48, and twice the warps are resident.
 template <int K>
 void launch_spmv_many(const Geom& g, const float* A, const float* x, const float* b, float* y, bool residual,
                       cudaStream_t s) {
     g_launches += 1;
     if (g.dim == 3) {
         if (g.nc == 3) launch_spmv_many_tile<3, 3, K, 16, 4, 2>(g, A, x, b, y, residual, s);
-        else launch_spmv_many_tile<3, 4, K, 16, 4, 2>(g, A, x, b, y, residual, s);
+        else launch_spmv_many_tile<3, 4, K, 16, 4, 2, 2>(g, A, x, b, y, residual, s);
     } else {
         if (g.nc == 2) launch_spmv_many_tile<2, 2, K, 32, 4, 1>(g, A, x, b, y, residual, s);
         else launch_spmv_many_tile<2, 3, K, 32, 4, 1>(g, A, x, b, y, residual, s);
