@@ -391,9 +391,12 @@ template <typename T>
 void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool residual, cudaStream_t s) {
     g_launches += 1;
     const bool lean = g.nc == g.dim;   // n_c = d: the vector problems (ALE extension)
-    // 3d with 4 unknowns a node: a node block of x is 16 or 32 aligned bytes (vector loads)
-    if (g.dim == 3 && !lean && (uintptr_t)x % 16 == 0)
-        pdl_launch(k_spmv_rows<T, 3, 4, true>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y,
+    // 3d FP64 with 4 unknowns a node: a node block of x is 32 aligned bytes (two
+    // 16-byte loads).  The FP32 product reads x entry by entry: its 16-byte x
+    // loads took the 32-register kernel past its registers (spills to local
+    // memory, 5% more DRAM traffic).
+    if (g.dim == 3 && !lean && sizeof(T) == 8 && (uintptr_t)x % 16 == 0)
+        pdl_launch(k_spmv_rows<T, 3, 4, sizeof(T) == 8>, dim3(blocks_for(g.nodes * g.nc, 256)), dim3(256), 0, s, g, A, x, b, y,
                    residual);
     else if (g.dim == 3)
         pdl_launch(lean ? k_spmv_rows<T, 3, 3> : k_spmv_rows<T, 3, 4>, dim3(blocks_for(g.nodes * g.nc, 256)),
