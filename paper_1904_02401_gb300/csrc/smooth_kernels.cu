@@ -17,6 +17,7 @@ namespace {
 using namespace elem;
 
 constexpr int kWaitSpins = 1 << 22;
+constexpr int64_t kLeanRingPatches = 4096;   // see launch_vanka_apply
 constexpr int kGatherDepth = 4;     // chunks of defect gathers in flight per CTA
 
 // y = A x  or  y = b - A x, one thread per node.  A in stencil layout.  Two
@@ -90,13 +91,13 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 // and there is no tail wave.  Row i of a patch is summed over the columns j in
 // ascending order with one fma per term, as in apply_patch, so the
 // corrections equal those of the other apply kernels bit for bit.
-template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1>
+template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1, int NC = DIM + 1>
 __global__ void __launch_bounds__(THREADS, 1)
 k_vanka_apply_ring(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __restrict__ d,
                    T* __restrict__ corr, int64_t npatch, const int32_t* __restrict__ ids) {
-    constexpr int NC = DIM + 1;
     constexpr int NP = ((DIM == 2) ? 9 : 27) * NC;
     constexpr int RW = NP / 27;                    // warps per patch
+    static_assert(NP % 27 == 0 && (THREADS / 32) % RW == 0, "a patch is whole warps of 27 rows");
     static_assert(PW == 1 || RW == 1, "two patches a warp only for 27-row patches");
     constexpr int CP = (THREADS / 32) / RW * PW;   // patches per chunk (PW patches per warp)
     constexpr int GD = kGatherDepth;
@@ -412,12 +413,12 @@ void launch_spmv(const Geom& g, const T* A, const T* x, const T* b, T* y, bool r
 // Launches the streaming apply on min(chunks, resident CTAs) CTAs.  The
 // resident count comes from the occupancy calculator for the kernel's shared
 // memory (cached per device and kernel instance).
-template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1>
+template <typename T, typename TS, int DIM, int STAGES, int THREADS, int PW = 1, int NC = DIM + 1>
 static void launch_ring(const Geom& g, const TS* inv, int64_t stride, const T* d, T* corr, cudaStream_t s,
                         int64_t npatch, const int32_t* ids) {
-    constexpr int CP = (THREADS / 32) / (DIM == 2 ? 1 : 4) * PW;
+    constexpr int CP = (THREADS / 32) / (((DIM == 2) ? 9 : 27) * NC / 27) * PW;
     const size_t smem = (size_t)STAGES * CP * stride * sizeof(TS);
-    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS, PW>;
+    auto kern = k_vanka_apply_ring<T, TS, DIM, STAGES, THREADS, PW, NC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     static int resident[kMaxDevices] = {};
     int dev = 0;
@@ -443,12 +444,22 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     // the bulk copies need 16-byte aligned chunks and the unpadded column
     // layout (stride at most n_p^2 rounded up to 16 bytes); FP64 and other
     // layouts use the warp kernel
-    const int np = g.dim == 2 ? 27 : 108;
-    const bool lean = g.nc == g.dim;   // n_c = d: warp kernel (the ring's chunks are 27-row slices)
-    const bool ring = !lean && sizeof(TS) <= 4 && ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
+    const int np = (g.dim == 2 ? 9 : 27) * g.nc;
+    // n_c = d: 2d patches (18 rows) take the warp kernel, the ring's warps
+    // being 27-row slices; 3d patches (81 rows, three warps) take the ring on
+    // levels of at most kLeanRingPatches patches (3d 32^3 extension solve
+    // 2.15 -> 1.61 ms) and the warp kernel above (with the ring up to the
+    // 48^3 level's 13,824 patches the 96^3 solve went from 16.7 to 17.5 ms)
+    const bool lean = g.nc == g.dim;
+    const bool ring = (!lean || (g.dim == 3 && npatch <= kLeanRingPatches)) && sizeof(TS) <= 4 &&
+                      ((uintptr_t)inv % 16 == 0) && ((stride * (int64_t)sizeof(TS)) % 16 == 0) &&
                       stride >= (int64_t)np * np && stride * (int64_t)sizeof(TS) <= (int64_t)np * np * sizeof(TS) + 16;
     if (npatch == 0) return;
     if constexpr (sizeof(TS) <= 4) {
+        if (ring && lean) {   // one 81-row patch a chunk (three warps), 4 stages
+            launch_ring<T, TS, 3, 4, 96, 1, 3>(g, inv, stride, d, corr, s, npatch, ids);
+            return;
+        }
         if (ring) {
             // 2d: about 70 KB of inverses in flight per CTA, 3 CTAs per SM.
             // 3d: one 108-unknown patch a chunk (4 warps), 3 stages of FP32
