@@ -84,6 +84,18 @@ WORKLOAD = "cfg2"
 WORKLOAD_DESC = WORKLOADS[WORKLOAD]
 
 
+def apply_kernel_name(problem, ncomp, precision):
+    """The library's finest-level apply kernel: the streaming ring for FP32 and
+    BF16 inverses, except 2d extension patches and 3d extension levels of more
+    than 4096 patches, which take the warp-per-patch kernel (as FP64 does)."""
+    patches = 1
+    for c in problem.n[:problem.dim]:
+        patches *= c // 2
+    lean = ncomp == problem.dim
+    ring = precision != 0 and (not lean or (problem.dim == 3 and patches <= 4096))
+    return "k_vanka_apply_ring" if ring else "k_vanka_apply"
+
+
 def workload_config(sysm):
     """The workload as both arms name it (no implementation details)."""
     return {"workload": WORKLOAD_DESC, "unknowns": int(sysm.unknowns), "levels": int(sysm.problem.levels),
@@ -490,7 +502,7 @@ def gpu_arm(args):
                         "engine": {1: "kernels", 2: "persistent", 3: "fused"}.get(infos[-1].engine, "?"),
                         "autotuned": {k: choice[k] for k in ("tail_patches", "tile_patches", "fused")},
                         "l2": "flushed before every solve (256 MB write, outside the per-solve events)"},
-        "roofline": {"kernel": ("k_vanka_apply" if args.precision == 0 else "k_vanka_apply_ring") +
+        "roofline": {"kernel": apply_kernel_name(sysm.problem, ncomp, args.precision) +
                                " (finest-level Vanka apply)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
