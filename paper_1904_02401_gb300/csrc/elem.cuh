@@ -43,9 +43,9 @@ template <typename T, typename TX> __device__ __forceinline__ T widen(TX v) { re
 template <> __device__ __forceinline__ double widen<double, float>(float v) { return widen_exact(v); }
 
 // N consecutive matrix entries at Ab (3d stencil layout: a node's block of
-// one position, or one row of it): float4 loads when N is a multiple of 4
-// (FP32), double2 loads when N is even (FP64), else entry by entry.  The 3d
-// layout keeps such runs 16-byte aligned (cudaMalloc'd base, blocks of 16
+// one position, or consecutive rows of it): float4 loads when N is a multiple
+// of 4 (FP32), double2 loads when N is even (FP64), else entry by entry.  The
+// 3d layout keeps such runs 16-byte aligned (cudaMalloc'd base, blocks of 16
 // entries, rows of 4).
 template <typename T, int N>
 __device__ __forceinline__ void load_arun(const T* __restrict__ Ab, T (&av)[N]) {
@@ -105,10 +105,10 @@ __device__ __forceinline__ int64_t patch_node(const Geom& g, int px, int py, int
 // not per position; the products are the same terms in the same order.
 // GB = 0 picks G: for a 2d matrix in global memory 9 (FP32) or 3 (FP64: 9
 // positions of 9 doubles and 3 neighbour values take over 200 registers), else
-// 1 (a matrix in shared memory has no latency to hide; in 3d the 16-entry
-// blocks already give each position 16 independent loads, and grouping
-// measured slower on GB300); kernels with few registers per thread pass a
-// smaller G.
+// 1 (a matrix in shared memory has no latency to hide; in 3d a position's
+// block is one contiguous run of the layout, read with vector loads, and
+// grouping positions measured slower on GB300); kernels with few registers
+// per thread pass a smaller G.
 template <typename T, int DIM, class XF, bool GLOBAL_A = true, int GB = 0, int NC>
 __device__ __forceinline__ void spmv_acc_f(const Geom& g, const T* __restrict__ A, XF&& xval, int64_t i,
                                            T (&acc)[NC]) {

@@ -83,7 +83,8 @@ k_vanka_apply(Geom g, const TS* __restrict__ inv, int64_t stride, const T* __res
 // Streaming apply for FP32 / BF16 inverses (2d and 3d): a persistent grid of
 // a few CTAs per SM walks the chunks c = blockIdx.x + k * gridDim.x; a chunk
 // is PW patches per warp in 2d (a lane sums row `lane` of each, the PW sums
-// side by side), or one patch per 4 warps (27 rows each) in 3d.  Each CTA
+// side by side), or in 3d one patch per n_c warps of 27 rows (4 warps for the
+// 108-unknown patches, 3 for the 81-unknown patches of n_c = d).  Each CTA
 // keeps STAGES chunk copies
 // of inverses (TMA bulk copies completing on one mbarrier per stage) and the
 // defect gathers of kGatherDepth chunks (cp.async) in flight, so neither the
@@ -448,7 +449,7 @@ void launch_vanka_apply(const Geom& g, const TS* inv, int64_t stride, const T* d
     // n_c = d: 2d patches (18 rows) take the warp kernel, the ring's warps
     // being 27-row slices; 3d patches (81 rows, three warps) take the ring on
     // levels of at most kLeanRingPatches patches (3d 32^3 extension solve
-    // 2.15 -> 1.61 ms) and the warp kernel above (with the ring up to the
+    // 2.12 -> 1.60 ms) and the warp kernel above (with the ring up to the
     // 48^3 level's 13,824 patches the 96^3 solve went from 16.7 to 17.5 ms)
     const bool lean = g.nc == g.dim;
     const bool ring = (!lean || (g.dim == 3 && npatch <= kLeanRingPatches)) && sizeof(TS) <= 4 &&
